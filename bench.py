@@ -1,0 +1,342 @@
+#!/usr/bin/env python3
+"""Throughput benchmark of the lattice Abelian-Higgs hot path on GB300.
+
+One bench step = one pass of the whole hot path over the workload: `diag_every`
+leapfrog steps (Eqs. up_pi, up_E, up_phi, up_A of arXiv:1809.00995) followed by
+one diagnostics pass (xi_L, xi_W, <v^2>_V, <v^2>_L, <v^2>_omega, Gauss residual).
+The default workload is a 1024^3 FP32 lattice in the matter era with s = 1,
+diagnostics every 50 steps (FP64 reductions); the metric is site-updates/s.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME] [--impl ours|reference]
+
+With N > 1 (torchrun, one rank per GPU) every rank evolves its own lattice
+(independent seeds): replicas, no collective on the data path; the barrier and
+the max-over-ranks timing follow the contract.  `--impl reference` times the
+FP64 CPU oracle on the host cores instead (rank 0 only).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOADS = {
+    # name: (N, precision, era, s, seed, diag_every, description)
+    "lattice1024_fp32_matter_s1": (1024, 0, 2, 1.0, 3, 50,
+                                   "1024^3 FP32 state, matter era a~tau^2, s=1, lambda0=2, e0=1, dx=0.5, "
+                                   "dt=0.1, random-phase init (Philox seed 3), diagnostics every 50 steps"),
+    "lattice256_fp32_rad_s0": (256, 0, 1, 0.0, 2, 20,
+                               "256^3 FP32 state, radiation era a~tau, s=0, seed 2, diagnostics every 20 steps"),
+    "lattice256_fp64_rad_s0": (256, 1, 1, 0.0, 2, 20,
+                               "256^3 FP64 state, radiation era a~tau, s=0, seed 2, diagnostics every 20 steps"),
+}
+DEFAULT = "lattice1024_fp32_matter_s1"
+BYTES_PER_SITE = {0: 80, 1: 160}      # one read + one write of the 10-real state
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "fused_step_traffic.json")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--workload", default=DEFAULT, choices=sorted(WORKLOADS))
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-plain", action="store_true", help="skip the plain FP64 comparison run")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
+    return ap.parse_args()
+
+
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("LOCAL_RANK", 0)), int(os.environ.get("WORLD_SIZE", 1))
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured (MEASURED_PEAKS.json hbm_gbs)"
+    except Exception:
+        return 6800.0, "fallback (6.8 TB/s)"
+
+
+def source_hash(path):
+    with open(path, "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
+
+
+def traffic_per_launch(n_sites):
+    """DRAM bytes per launch of the fused step from the committed ncu summary, if it
+    was taken on the current kernel source."""
+    try:
+        with open(TRAFFIC_FILE) as f:
+            d = json.load(f)
+        src = os.path.join(ROOT, "paper_1809_00995_gb300", "csrc", "k_fused.cu")
+        if d.get("k_fused_sha256_16") != source_hash(src):
+            return None
+        return d["dram_bytes_per_site"] * n_sites
+    except Exception:
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms in the background."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, uuid=None):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        cmd = ["nvidia-smi", "--query-gpu=" + self.Q, "--format=csv,noheader,nounits", "-lms", "200"]
+        if uuid:
+            cmd += ["-i", uuid]
+        try:
+            self.p = subprocess.Popen(cmd, stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return None
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except Exception:
+            self.p.kill()
+        self.f.flush()
+        rows = []
+        with open(self.f.name) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9 and parts[1].replace(".", "").isdigit():
+                    rows.append(parts)
+        os.unlink(self.f.name)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": float(rows[0][2]), "reasons": reasons,
+                "samples": len(rows), "power_w_max": max(float(r[3]) for r in rows if r[3].replace(".", "").isdigit())}
+
+
+def cpu_oracle_rate(wl, budget_s=12.0, M=48):
+    """Site-updates/s of the FP64 CPU oracle on a bounded sample of the workload: an
+    M^3 window of the same lattice (same init, same couplings), stepped until about
+    budget_s seconds have passed, plus one diagnostics pass weighted by 1/diag_every."""
+    import oracle as O
+    N, prec, era, s, seed, diag_every, _ = WORKLOADS[wl]
+    p = O.Params(N=N, era=era, s=s, seed=seed)
+    f = O.init(p, M=M, origin=(N // 3, N // 5, N // 7))
+    O.evolve(p, f, 0, 1)                       # warm (threads, pages)
+    n, t0 = 0, time.perf_counter()
+    while True:
+        O.evolve(p, f, 1 + n, 1)
+        n += 1
+        if time.perf_counter() - t0 > budget_s * 0.8:
+            break
+    t_step = (time.perf_counter() - t0) / n
+    t1 = time.perf_counter()
+    O.observables(p, f, 1 + n)
+    t_diag = time.perf_counter() - t1
+    rate = M ** 3 / (t_step + t_diag / diag_every)
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return rate, cores, "%d^3 window of the %d^3 workload, %d oracle steps (%.2f s/step) + 1 diagnostics pass " \
+                        "(%.2f s) weighted 1/%d" % (M, N, n, t_step, t_diag, diag_every)
+
+
+def reference_arm(a, wl, rank, world):
+    """The CPU oracle as it stands, timed on the host cores; rank 0 only."""
+    if rank != 0:
+        return
+    import oracle as O
+    N, prec, era, s, seed, diag_every, desc = WORKLOADS[wl]
+    M = 40
+    p = O.Params(N=N, era=era, s=s, seed=seed)
+    f = O.init(p, M=M, origin=(N // 3, N // 5, N // 7))
+    n = 0
+
+    def one():
+        nonlocal n
+        O.evolve(p, f, n, diag_every)
+        n += diag_every
+        O.observables(p, f, n)
+
+    for _ in range(a.warmup):
+        one()
+    t0 = time.perf_counter()
+    for _ in range(a.steps):
+        one()
+    t = time.perf_counter() - t0
+    value = M ** 3 * diag_every * a.steps / t
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    sample = "%d^3 window of the workload per step: %d oracle leapfrog steps + 1 diagnostics pass" % (M, diag_every)
+    print(json.dumps({
+        "impl": "reference", "metric": "site-updates/s", "value": value, "unit": "site-updates/s",
+        "n_gpus": world, "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1e3 * t / a.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": wl, "description": desc, "N": N, "diag_every": diag_every},
+        "cpu_baseline": {"kind": "oracle", "cores": cores, "sample": sample, "value": value, "unit": "site-updates/s"},
+        "e2e": {"value": value, "unit": "site-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+def main():
+    a = parse()
+    rank, local_rank, world = dist_env()
+    wl = a.workload
+    if a.impl == "reference":
+        return reference_arm(a, wl, rank, world)
+
+    import torch
+    import paper_1809_00995_gb300 as ah
+    from paper_1809_00995_gb300 import _build
+
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    if rank == 0:
+        _build.build()
+    if dist:
+        dist.barrier()
+
+    def barrier():
+        if dist:
+            dist.barrier()
+
+    N, prec, era, s, seed, diag_every, desc = WORKLOADS[wl]
+    n_sites = N ** 3
+    stream = torch.cuda.Stream()
+    g = ah.Sim(N, precision=prec, kernel=ah.AH_KERNEL_FUSED, era=era, s=s, seed=seed + 1000 * rank)
+    ah.ah_set_stream(g.h, stream.cuda_stream)
+    info = g.info
+
+    def bench_step(ev_a=None, ev_b=None):
+        if ev_a is not None:
+            ev_a.record(stream)
+        g.step(diag_every)
+        if ev_b is not None:
+            ev_b.record(stream)
+        return g.observables()
+
+    for _ in range(a.warmup):
+        obs = bench_step()
+    torch.cuda.synchronize()
+
+    try:
+        uuid = "GPU-" + str(torch.cuda.get_device_properties(local_rank).uuid)
+    except Exception:
+        uuid = None
+    sampler = ClockSampler(uuid) if rank == 0 else None
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(a.steps)]
+    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    torch.cuda.synchronize()
+    start.record(stream)
+    for k in range(a.steps):
+        obs = bench_step(*ev[k])
+    end.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clocks = sampler.stop() if sampler else None
+    t_ms = start.elapsed_time(end)
+    step_ms = sum(x.elapsed_time(y) for x, y in ev)
+    t_max = t_ms
+    if dist:
+        tt = torch.tensor([t_ms], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_max = float(tt.item())
+    value = world * n_sites * diag_every * a.steps / (t_max / 1e3)
+
+    # end to end through the public C ABI: host-side timing, synchronous
+    # observables copied to a host struct every bench step
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(a.steps):
+        ah.ah_step(g.h, diag_every)
+        obs_e2e = ah.ah_observables(g.h)
+    t_e2e = time.perf_counter() - t0
+    e2e_value = world * n_sites * diag_every * a.steps / t_e2e
+    import ctypes
+    d2h = ctypes.sizeof(ah.ah_obs)
+    final_obs = obs_e2e
+    g.close()
+
+    avg_launch_s = step_ms / 1e3 / (a.steps * diag_every)
+    alg_bytes = BYTES_PER_SITE[prec] * n_sites
+    peak, peak_src = peaks()
+    achieved = alg_bytes / avg_launch_s / 1e9
+    tr = traffic_per_launch(n_sites)
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": tr, "kernel": "k_fused (one leapfrog step)", "peak_source": peak_src,
+                "alg_bytes_per_launch": alg_bytes, "avg_launch_ms": avg_launch_s * 1e3,
+                "step_share_of_time": step_ms / t_ms}
+
+    plain = None
+    if rank == 0 and not a.no_plain:
+        # the plain FP64 single-lattice path (the paper's three-kernel structure) on
+        # the same lattice size: the speed-up denominator
+        try:
+            h = ah.Sim(N, precision=ah.AH_FP64, kernel=ah.AH_KERNEL_PLAIN, era=era, s=s, seed=seed)
+            ah.ah_set_stream(h.h, stream.cuda_stream)
+            h.step(1)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            np_ = 3
+            e0.record(stream)
+            h.step(np_)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            tp = e0.elapsed_time(e1) / 1e3
+            h.close()
+            pv = n_sites * np_ / tp
+            plain = {"value": pv, "unit": "site-updates/s", "steps": np_, "dtype": "f64",
+                     "kernel": "plain (Pi kick, E kick, drift)", "speedup_of_value_over_plain": value / pv}
+        except ah.AhError as e:
+            plain = {"unavailable": str(e)}
+
+    cpu = None
+    if rank == 0 and world == 1 and not a.no_cpu:
+        rate, cores, sample = cpu_oracle_rate(wl)
+        cpu = {"value": rate, "unit": "site-updates/s", "cores": cores, "kind": "oracle", "sample": sample}
+
+    if rank == 0:
+        line = {
+            "metric": "site-updates/s", "value": value, "unit": "site-updates/s", "n_gpus": world,
+            "steps": a.steps, "warmup": a.warmup, "ms_per_step": t_max / a.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32" if prec == 0 else "f64", "data": "synthetic",
+            "config": {"workload": wl, "description": desc, "N": N, "diag_every": diag_every,
+                       "leapfrog_steps_per_bench_step": diag_every,
+                       "l2": "inputs larger than L2 (%.1f GB state)" % (info["state_bytes"] / 1e9),
+                       "parallelism": "replicas" if world > 1 else "single"},
+            "hbm_gbs_effective": achieved,
+            "roofline": roofline,
+            "cpu_baseline": cpu,
+            "plain_fp64": plain,
+            "e2e": {"value": e2e_value, "unit": "site-updates/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": d2h},
+            "gpu_launches": a.steps * (diag_every * info["step_launches"] + 2),
+            "clocks": clocks,
+            "final_obs": {k: final_obs[k] for k in ("step", "tau", "xi_L", "xi_W", "v2_V", "v2_L", "v2_omega",
+                                                     "gauss_rel", "max_abs_theta")},
+        }
+        print(json.dumps(line))
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,197 @@
+/*
+ * ah.h -- C ABI of the GB300 lattice Abelian-Higgs library.
+ *
+ * The library evolves a periodic N^3 lattice of the U(1) Abelian-Higgs model
+ * in conformal time with the staggered leapfrog of Correia & Martins,
+ * arXiv:1809.00995 (Sec. 2, Eqs. up_pi, up_E, up_phi, up_A, with the
+ * s-dependent couplings of Eq. 7 and the random-phase initial state), and
+ * computes the network diagnostics of the same section (xi_L and <v^2>_X of
+ * Eqs. defXiV2/defR, the winding length xi_W of Eq. 9, <v^2>_omega of
+ * Eq. defEoS) plus the Gauss-law residual.  All compute runs in CUDA kernels
+ * on one GPU (sm_103a); there is no CPU fallback.
+ *
+ * Conventions (all entry points):
+ *  - Every call returns an ah_status (AH_OK = 0) and never aborts the
+ *    process; ah_last_error() gives a thread-local message for the last
+ *    failure on the calling thread.
+ *  - Pointers are host pointers unless stated otherwise.  Output structs and
+ *    buffers are owned by the caller; the library owns all device memory of a
+ *    simulation and frees it in ah_destroy.
+ *  - Lattice site (x, y, z), 0 <= x, y, z < N, has linear index
+ *    x + N*(y + N*z) (x fastest); boundaries are periodic.
+ *  - Field components, in this order wherever 10 of them are packed:
+ *    0 phi.re, 1 phi.im, 2 Pi.re, 3 Pi.im, 4..6 theta_1..3, 7..9 E_1..3,
+ *    where theta_i = e dx A_i is the phase of the link x -> x + k_i (Eq. 3)
+ *    and E_i = d theta_i / d eta its conjugate.  At integer step n the state
+ *    holds phi^n, theta^n, Pi^{n-1/2}, E^{n-1/2}.
+ *  - Background: a(tau) = (tau / tau_ref)^alpha with alpha = 0, 1, 2 for
+ *    Minkowski, radiation, matter; e = e0 a^(s-1), lambda = lambda0 a^(2(s-1))
+ *    (Eq. 7); tau_n = tau0 + n dt.
+ */
+#ifndef AH_H
+#define AH_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum ah_status {
+    AH_OK = 0,
+    AH_ERR_ARG = 1,        /* invalid argument or configuration          */
+    AH_ERR_OOM = 2,        /* device or host allocation failed           */
+    AH_ERR_CUDA = 3,       /* a CUDA runtime call or launch failed       */
+    AH_ERR_UNSTABLE = 4,   /* configuration violates leapfrog stability  */
+    AH_ERR_NONFINITE = 5,  /* diagnostics found Inf/NaN in the state     */
+    AH_ERR_TIMEOUT = 6,    /* a bounded device or host wait gave up      */
+    AH_ERR_BUSY = 7,       /* resource in use (server full, call pending)*/
+    AH_ERR_CANCELLED = 8,  /* request was cancelled                      */
+    AH_ERR_NOTFOUND = 9    /* unknown request id                         */
+} ah_status;
+
+enum { AH_MINKOWSKI = 0, AH_RADIATION = 1, AH_MATTER = 2 };
+enum { AH_FP32 = 0, AH_FP64 = 1 };
+/* Kernel family for the leapfrog step.
+ *  PLAIN: the paper's three-kernel structure (Pi kick, E kick, drift),
+ *         one thread per site, all loads from global memory.
+ *  FUSED: one z-marching kernel per step: both kicks and both drifts fused,
+ *         shared-memory XY tiles, link exponentials computed once per site,
+ *         ping-pong phi/theta buffers.
+ *  AUTO:  FUSED. */
+enum { AH_KERNEL_AUTO = 0, AH_KERNEL_PLAIN = 1, AH_KERNEL_FUSED = 2 };
+
+typedef struct ah_config {
+    int32_t N;            /* lattice side, 4 <= N <= 2048                         */
+    int32_t era;          /* AH_MINKOWSKI, AH_RADIATION, AH_MATTER                 */
+    int32_t precision;    /* AH_FP32 or AH_FP64 field state and stencil arithmetic */
+    int32_t kernel;       /* AH_KERNEL_*                                           */
+    double dx;            /* lattice spacing, > 0                                   */
+    double dt;            /* time step, 0 < dt <= dx / sqrt(3) (Courant)            */
+    double s;             /* coupling exponent of Eq. 7                             */
+    double lambda0;       /* scalar self-coupling, >= 0                             */
+    double e0;            /* gauge coupling, > 0                                    */
+    double sigma;         /* vacuum expectation value, > 0                         */
+    double tau0;          /* conformal time at step 0, > 0 unless Minkowski         */
+    double tau_end;       /* end of the run (default N dx / 2, half light-crossing) */
+    double tau_ref;       /* normalisation a(tau_ref) = 1 (default tau_end)         */
+    uint64_t seed;        /* Philox-4x32-10 key of the random-phase initial state   */
+    int32_t diag_every;   /* diagnostic cadence used by batch and serve (0: end only) */
+    int32_t flags;        /* reserved, must be 0                                   */
+} ah_config;
+
+/* Network observables at one integer step (Sec. 2).  sums[] are the raw FP64
+ * site sums, in the order:
+ *   0 L, 1 rho, 2 p, 3 K=|Pi|^2, 4 G2=|D phi|^2, 5 V, 6 E_el, 7 B_mag,
+ *   8 K V, 9 G2 V, 10 K L, 11 G2 L, 12 p L, 13 rho L, 14 G^2, 15 scale^2
+ * with, per site at tau_n,
+ *   G2 = dx^-2 sum_i |e^{i theta_i} phi^{x+i} - phi^x|^2,
+ *   V = a^2 lambda/4 (|phi|^2 - sigma^2)^2, E_el = sum_i E_i^2 / (2 e^2 a^2 dx^2),
+ *   B_mag = sum_{i<j} (1 - cos Xi_ij) / (e^2 a^2 dx^4),
+ *   L = K - G2 - V + E_el - B_mag, rho = K + G2 + V + E_el + B_mag,
+ *   p = K - G2/3 - V + (E_el + B_mag)/3,
+ *   G = e_-^-2 sum_i (E_i^x - E_i^{x-i}) + 2 dx^2 a_-^2 Im(conj(phi) Pi)
+ *       (Gauss residual, a_- and e_- at tau_n - dt/2; scale = |term 1| + |term 2|).
+ * Derived: xi_L = sqrt(-2 pi sigma^2 / L_mean); xi_W = sqrt(n_sites dx^3 / l_W)
+ * with l_W = (pi/6) dx sum_abs_W; <v^2>_X = 2R_X/(1+R_X), R_V = sums[8]/sums[9],
+ * R_L = sums[10]/sums[11]; v2_omega = (1 + 3 p_over_rho_L)/2 with
+ * p_over_rho_L = sums[12]/sums[13]; energy = dx^3 sums[1].  Zero denominators
+ * follow IEEE rules (Inf/NaN are reported, not trapped). */
+typedef struct ah_obs {
+    double tau, a;
+    int64_t step;
+    int64_t n_sites;
+    double L_mean, xi_L, xi_W;
+    int64_t n_pierced;           /* plaquettes with W != 0                     */
+    int64_t sum_abs_W;           /* sum of |W| over all plaquettes             */
+    double R_V, R_L, v2_V, v2_L, p_over_rho_L, v2_omega;
+    double gauss_rms, gauss_max, gauss_rel, energy, max_abs_theta;
+    double sums[16];
+    int64_t wind_abs_plane[3];   /* sum |W| by orientation 12, 13, 23          */
+    int64_t wind_plane[3];       /* signed sums by orientation                 */
+    int64_t nonfinite;           /* sites whose L, rho, p or G is not finite   */
+} ah_obs;
+
+typedef struct ah_sim ah_sim;
+
+/* Version of this ABI (bumped on any change of a struct or signature). */
+int ah_abi_version(void);
+
+/* Fill *cfg with the defaults for an N^3 lattice: FP32, radiation era, s = 0,
+ * lambda0 = 2, e0 = 1, sigma = 1, dx = 0.5, dt = 0.1, tau0 = 1,
+ * tau_end = N dx / 2, tau_ref = tau_end, seed 1, kernel AUTO. */
+void ah_config_default(ah_config *cfg, int32_t N);
+
+/* Create a simulation with the defaults above, overriding N, dx, dt, era, s,
+ * lambda0, e0 and seed; initial state: phi = sigma e^{i 2 pi u}, u from
+ * Philox-4x32-10 (key = seed, counter = (0, 0, site index)), Pi = theta = E = 0
+ * (Sec. 2).  Returns NULL on error (see ah_last_error). */
+ah_sim *ah_create(int32_t N, double dx, double dt, int32_t era, double s,
+                  double lambda0, double e0, uint64_t seed);
+
+/* Create from a full configuration.  Validates the arguments (AH_ERR_ARG),
+ * rejects a stiff scalar mode that breaks leapfrog stability,
+ * sqrt(lambda0) sigma max_tau a(tau)^s dt >= 1, with AH_ERR_UNSTABLE, allocates
+ * the state on the current CUDA device (AH_ERR_OOM) and writes the initial
+ * state.  *out receives the handle. */
+ah_status ah_create_ex(const ah_config *cfg, ah_sim **out);
+
+/* Enqueue nsteps leapfrog steps (Eqs. up_pi, up_E, up_phi, up_A) on the
+ * simulation's stream; returns without waiting.  nsteps >= 0. */
+ah_status ah_step(ah_sim *sim, int64_t nsteps);
+
+/* Compute the observables of the current state over the whole lattice and
+ * write them to *out (waits for the simulation's stream).  The per-site
+ * values and all sums are FP64 whatever the state precision.  Returns
+ * AH_ERR_NONFINITE (with *out filled) if any site is not finite. */
+ah_status ah_observables(ah_sim *sim, ah_obs *out);
+
+/* Same over the sub-box [x0, x0+nx) x [y0, y0+ny) x [z0, z0+nz), taken mod N
+ * (plaquettes and differences still reach the neighbours outside the box). */
+ah_status ah_observables_box(ah_sim *sim, int32_t x0, int32_t y0, int32_t z0,
+                             int32_t nx, int32_t ny, int32_t nz, ah_obs *out);
+
+/* Copy the state of the window [x0, x0+nx) x ... (mod N) to host memory `out`
+ * as FP64: 10 components, each nz*ny*nx with x fastest (10*nx*ny*nz doubles).
+ * Waits for the simulation's stream. */
+ah_status ah_get_fields(ah_sim *sim, int32_t x0, int32_t y0, int32_t z0,
+                        int32_t nx, int32_t ny, int32_t nz, double *out);
+
+/* Replace the whole state by host FP64 data `in` (10*N^3 doubles, layout as
+ * above; rounded to the state precision) and set the step counter. */
+ah_status ah_set_fields(ah_sim *sim, const double *in, int64_t step);
+
+/* Use the given cudaStream_t (as void*; NULL = the library's own stream) for
+ * all later work of this simulation. */
+ah_status ah_set_stream(ah_sim *sim, void *cuda_stream);
+
+/* Wait for all work enqueued for this simulation. */
+ah_status ah_sync(ah_sim *sim);
+
+/* Current integer step n and conformal time tau_n. */
+int64_t ah_get_step(const ah_sim *sim);
+double ah_get_tau(const ah_sim *sim);
+
+/* Information for measurement: bytes of device state, the algorithmic bytes
+ * one leapfrog step must move (one read and one write of the 10-component
+ * state: 80 B per site in FP32, 160 B in FP64), and the kernel in use. */
+typedef struct ah_info {
+    int64_t N, n_sites;
+    int32_t precision, kernel;
+    int64_t state_bytes;
+    int64_t step_bytes;
+    int64_t step_launches;   /* kernel launches per leapfrog step */
+} ah_info;
+ah_status ah_get_info(const ah_sim *sim, ah_info *out);
+
+/* Free all resources of the simulation (NULL-safe). */
+void ah_destroy(ah_sim *sim);
+
+/* Message for the last failed call on this thread ("" if none). */
+const char *ah_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* AH_H */

@@ -1,0 +1,278 @@
+"""Python binding of the GB300 lattice Abelian-Higgs library (libah.so).
+
+Thin ctypes marshalling over the C ABI of include/ah.h, with the same names
+(``ah_create``, ``ah_step``, ``ah_observables`` ...).  Every step of the
+method runs in the library's CUDA kernels; there is no Python or CPU
+fallback: importing works anywhere, but the first call that needs the library
+raises if libah.so is missing or no CUDA device is present.
+
+``Sim`` wraps a handle for convenience (context manager, numpy field access).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from . import _build
+
+_lock = threading.Lock()
+_lib = None
+
+AH_OK, AH_ERR_ARG, AH_ERR_OOM, AH_ERR_CUDA, AH_ERR_UNSTABLE = 0, 1, 2, 3, 4
+AH_ERR_NONFINITE, AH_ERR_TIMEOUT, AH_ERR_BUSY, AH_ERR_CANCELLED, AH_ERR_NOTFOUND = 5, 6, 7, 8, 9
+AH_MINKOWSKI, AH_RADIATION, AH_MATTER = 0, 1, 2
+AH_FP32, AH_FP64 = 0, 1
+AH_KERNEL_AUTO, AH_KERNEL_PLAIN, AH_KERNEL_FUSED = 0, 1, 2
+
+SUM_NAMES = ("L", "rho", "p", "K", "G2", "V", "Eel", "B", "KV", "G2V", "KL", "G2L", "pL", "rhoL",
+             "gauss2", "gscale2")
+
+
+class AhError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__("ah status %d: %s" % (status, msg))
+        self.status = status
+
+
+class ah_config(ctypes.Structure):
+    _fields_ = [("N", ctypes.c_int32), ("era", ctypes.c_int32), ("precision", ctypes.c_int32),
+                ("kernel", ctypes.c_int32), ("dx", ctypes.c_double), ("dt", ctypes.c_double),
+                ("s", ctypes.c_double), ("lambda0", ctypes.c_double), ("e0", ctypes.c_double),
+                ("sigma", ctypes.c_double), ("tau0", ctypes.c_double), ("tau_end", ctypes.c_double),
+                ("tau_ref", ctypes.c_double), ("seed", ctypes.c_uint64), ("diag_every", ctypes.c_int32),
+                ("flags", ctypes.c_int32)]
+
+
+class ah_obs(ctypes.Structure):
+    _fields_ = [("tau", ctypes.c_double), ("a", ctypes.c_double), ("step", ctypes.c_int64),
+                ("n_sites", ctypes.c_int64), ("L_mean", ctypes.c_double), ("xi_L", ctypes.c_double),
+                ("xi_W", ctypes.c_double), ("n_pierced", ctypes.c_int64), ("sum_abs_W", ctypes.c_int64),
+                ("R_V", ctypes.c_double), ("R_L", ctypes.c_double), ("v2_V", ctypes.c_double),
+                ("v2_L", ctypes.c_double), ("p_over_rho_L", ctypes.c_double), ("v2_omega", ctypes.c_double),
+                ("gauss_rms", ctypes.c_double), ("gauss_max", ctypes.c_double), ("gauss_rel", ctypes.c_double),
+                ("energy", ctypes.c_double), ("max_abs_theta", ctypes.c_double),
+                ("sums", ctypes.c_double * 16), ("wind_abs_plane", ctypes.c_int64 * 3),
+                ("wind_plane", ctypes.c_int64 * 3), ("nonfinite", ctypes.c_int64)]
+
+    def as_dict(self) -> dict:
+        d = {}
+        for name, _ in self._fields_:
+            v = getattr(self, name)
+            d[name] = list(v) if hasattr(v, "__len__") else v
+        d["sum"] = dict(zip(SUM_NAMES, d["sums"]))
+        return d
+
+
+class ah_info(ctypes.Structure):
+    _fields_ = [("N", ctypes.c_int64), ("n_sites", ctypes.c_int64), ("precision", ctypes.c_int32),
+                ("kernel", ctypes.c_int32), ("state_bytes", ctypes.c_int64), ("step_bytes", ctypes.c_int64),
+                ("step_launches", ctypes.c_int64)]
+
+
+_SIGS = {
+    "ah_abi_version": ([], ctypes.c_int),
+    "ah_last_error": ([], ctypes.c_char_p),
+    "ah_config_default": ([ctypes.POINTER(ah_config), ctypes.c_int32], None),
+    "ah_create": ([ctypes.c_int32, ctypes.c_double, ctypes.c_double, ctypes.c_int32, ctypes.c_double,
+                   ctypes.c_double, ctypes.c_double, ctypes.c_uint64], ctypes.c_void_p),
+    "ah_create_ex": ([ctypes.POINTER(ah_config), ctypes.POINTER(ctypes.c_void_p)], ctypes.c_int),
+    "ah_step": ([ctypes.c_void_p, ctypes.c_int64], ctypes.c_int),
+    "ah_observables": ([ctypes.c_void_p, ctypes.POINTER(ah_obs)], ctypes.c_int),
+    "ah_observables_box": ([ctypes.c_void_p] + [ctypes.c_int32] * 6 + [ctypes.POINTER(ah_obs)], ctypes.c_int),
+    "ah_get_fields": ([ctypes.c_void_p] + [ctypes.c_int32] * 6 + [ctypes.c_void_p], ctypes.c_int),
+    "ah_set_fields": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64], ctypes.c_int),
+    "ah_set_stream": ([ctypes.c_void_p, ctypes.c_void_p], ctypes.c_int),
+    "ah_sync": ([ctypes.c_void_p], ctypes.c_int),
+    "ah_get_step": ([ctypes.c_void_p], ctypes.c_int64),
+    "ah_get_tau": ([ctypes.c_void_p], ctypes.c_double),
+    "ah_get_info": ([ctypes.c_void_p, ctypes.POINTER(ah_info)], ctypes.c_int),
+    "ah_destroy": ([ctypes.c_void_p], None),
+}
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load libah.so (building it with nvcc first if it is missing or stale)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if build_if_missing:
+                _build.build()
+            if not os.path.exists(_build.LIB):
+                raise RuntimeError("libah.so not built (%s); run paper_1809_00995_gb300._build.build()"
+                                   % _build.LIB)
+            lib = ctypes.CDLL(_build.LIB)
+            for name, (args, res) in _SIGS.items():
+                fn = getattr(lib, name)
+                fn.argtypes = args
+                fn.restype = res
+            _lib = lib
+    return _lib
+
+
+def exported_symbols():
+    return list(_SIGS)
+
+
+def _check(status: int):
+    if status != AH_OK:
+        raise AhError(status, load().ah_last_error().decode())
+
+
+# ---- same-name wrappers of the C ABI -------------------------------------------------
+def ah_abi_version() -> int:
+    return load().ah_abi_version()
+
+
+def ah_last_error() -> str:
+    return load().ah_last_error().decode()
+
+
+def ah_config_default(N: int) -> ah_config:
+    c = ah_config()
+    load().ah_config_default(ctypes.byref(c), N)
+    return c
+
+
+def ah_create(N, dx, dt, era, s, lambda0, e0, seed) -> int:
+    h = load().ah_create(N, dx, dt, era, s, lambda0, e0, seed)
+    if not h:
+        raise AhError(-1, ah_last_error())
+    return h
+
+
+def ah_create_ex(cfg: ah_config) -> int:
+    h = ctypes.c_void_p()
+    _check(load().ah_create_ex(ctypes.byref(cfg), ctypes.byref(h)))
+    return h.value
+
+
+def ah_step(h, nsteps: int):
+    _check(load().ah_step(h, nsteps))
+
+
+def ah_observables(h, check_finite: bool = True) -> dict:
+    o = ah_obs()
+    st = load().ah_observables(h, ctypes.byref(o))
+    if st != AH_OK and not (st == AH_ERR_NONFINITE and not check_finite):
+        _check(st)
+    return o.as_dict()
+
+
+def ah_observables_box(h, x0, y0, z0, nx, ny, nz) -> dict:
+    o = ah_obs()
+    _check(load().ah_observables_box(h, x0, y0, z0, nx, ny, nz, ctypes.byref(o)))
+    return o.as_dict()
+
+
+def ah_get_fields(h, x0, y0, z0, nx, ny, nz) -> np.ndarray:
+    out = np.empty((10, nz, ny, nx), dtype=np.float64)
+    _check(load().ah_get_fields(h, x0, y0, z0, nx, ny, nz, out.ctypes.data))
+    return out
+
+
+def ah_set_fields(h, fields: np.ndarray, step: int = 0):
+    f = np.ascontiguousarray(fields, dtype=np.float64)
+    _check(load().ah_set_fields(h, f.ctypes.data, step))
+
+
+def ah_set_stream(h, stream_ptr: int | None):
+    _check(load().ah_set_stream(h, stream_ptr or None))
+
+
+def ah_sync(h):
+    _check(load().ah_sync(h))
+
+
+def ah_get_step(h) -> int:
+    return load().ah_get_step(h)
+
+
+def ah_get_tau(h) -> float:
+    return load().ah_get_tau(h)
+
+
+def ah_get_info(h) -> dict:
+    i = ah_info()
+    _check(load().ah_get_info(h, ctypes.byref(i)))
+    return {n: getattr(i, n) for n, _ in i._fields_}
+
+
+def ah_destroy(h):
+    if h:
+        load().ah_destroy(h)
+
+
+# ---- convenience ------------------------------------------------------------------
+def config(N: int, **kw) -> ah_config:
+    """ah_config with the library defaults for N, fields overridden by keyword."""
+    c = ah_config_default(N)
+    if "tau_end" not in kw and "dx" in kw:
+        kw["tau_end"] = N * kw["dx"] / 2.0
+    if "tau_ref" not in kw:
+        kw["tau_ref"] = kw.get("tau_end", c.tau_end)
+    for k, v in kw.items():
+        if not hasattr(c, k):
+            raise AttributeError(k)
+        setattr(c, k, v)
+    return c
+
+
+class Sim:
+    """Owning wrapper of one simulation handle."""
+
+    def __init__(self, N: int, **kw):
+        self.cfg = config(N, **kw)
+        self.h = ah_create_ex(self.cfg)
+        self.N = N
+
+    def step(self, n: int = 1):
+        ah_step(self.h, n)
+        return self
+
+    def observables(self, check_finite=True) -> dict:
+        return ah_observables(self.h, check_finite)
+
+    def observables_box(self, x0, y0, z0, nx, ny, nz) -> dict:
+        return ah_observables_box(self.h, x0, y0, z0, nx, ny, nz)
+
+    def fields(self, x0=0, y0=0, z0=0, nx=None, ny=None, nz=None) -> np.ndarray:
+        N = self.N
+        return ah_get_fields(self.h, x0, y0, z0, nx or N, ny or N, nz or N)
+
+    def set_fields(self, f: np.ndarray, step: int = 0):
+        ah_set_fields(self.h, f, step)
+
+    def sync(self):
+        ah_sync(self.h)
+
+    @property
+    def n(self) -> int:
+        return ah_get_step(self.h)
+
+    @property
+    def info(self) -> dict:
+        return ah_get_info(self.h)
+
+    def close(self):
+        if self.h:
+            ah_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

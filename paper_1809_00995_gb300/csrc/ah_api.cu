@@ -1,0 +1,474 @@
+// ah_api.cu -- host side of the C ABI declared in include/ah.h.
+//
+// Owns the device state of each simulation, computes the per-step FP64
+// coefficients of the leapfrog (Eqs. up_pi, up_E with the Eq. 7 couplings)
+// and of the diagnostics, and enqueues the kernels.  No arithmetic of the
+// method runs on the host besides those scalar coefficients and the final
+// combination of the FP64 sums into the observables.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "../../include/ah.h"
+#include "ah_internal.cuh"
+
+using namespace ah;
+
+namespace {
+
+thread_local std::string g_err;
+
+ah_status fail(ah_status st, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return st;
+}
+
+#define AH_CUDA(call)                                                                  \
+    do {                                                                               \
+        cudaError_t e_ = (call);                                                       \
+        if (e_ != cudaSuccess)                                                         \
+            return fail(e_ == cudaErrorMemoryAllocation ? AH_ERR_OOM : AH_ERR_CUDA,    \
+                        "%s failed: %s", #call, cudaGetErrorString(e_));               \
+    } while (0)
+
+// Background of Sec. 2: a(tau) = (tau/tau_ref)^alpha, alpha = 0, 1, 2.
+double scale_factor(const ah_config &c, double tau)
+{
+    const double r = tau / c.tau_ref;
+    if (c.era == AH_RADIATION) return r;
+    if (c.era == AH_MATTER) return r * r;
+    return 1.0;
+}
+double coupling_e(const ah_config &c, double a) { return c.e0 * std::pow(a, c.s - 1.0); }
+double coupling_lambda(const ah_config &c, double a) { return c.lambda0 * std::pow(a, 2.0 * (c.s - 1.0)); }
+double tau_of(const ah_config &c, int64_t n) { return c.tau0 + (double)n * c.dt; }
+
+// Kick coefficients of step n (Eqs. up_pi, up_E), FP64, half-step scale
+// factors evaluated at tau_n -+ dt/2.
+template <typename real>
+KickCoef<real> kick_coef(const ah_config &c, int64_t n)
+{
+    const double tn = tau_of(c, n), tm = tn - 0.5 * c.dt, tp = tn + 0.5 * c.dt;
+    const double an = scale_factor(c, tn), am = scale_factor(c, tm), ap = scale_factor(c, tp);
+    const double en = coupling_e(c, an), em = coupling_e(c, am), ep = coupling_e(c, ap);
+    const double lam = coupling_lambda(c, an);
+    const double idx2 = 1.0 / (c.dx * c.dx);
+    KickCoef<real> k;
+    k.c_damp = (real)((am / ap) * (am / ap));
+    k.c_pot = (real)(c.dt * (an * an / ap) * (an * an / ap) * lam * 0.5);
+    k.c_lap = (real)(c.dt * idx2 * (an / ap) * (an / ap));
+    k.c_edamp = (real)((ep / em) * (ep / em));
+    k.c_cur = (real)(2.0 * c.dt * an * an * ep * ep);
+    k.c_curl = (real)(c.dt * idx2 * (ep / en) * (ep / en));
+    k.dt = (real)c.dt;
+    k.sigma2 = (real)(c.sigma * c.sigma);
+    return k;
+}
+
+DiagCoef diag_coef(const ah_config &c, int64_t n)
+{
+    const double tn = tau_of(c, n), tm = tn - 0.5 * c.dt;
+    const double an = scale_factor(c, tn), am = scale_factor(c, tm);
+    const double en = coupling_e(c, an), em = coupling_e(c, am);
+    const double lam = coupling_lambda(c, an);
+    const double dx2 = c.dx * c.dx, e2a2 = en * en * an * an;
+    DiagCoef d;
+    d.inv_dx2 = 1.0 / dx2;
+    d.v_coef = an * an * lam / 4.0;
+    d.eel_coef = 1.0 / (2.0 * e2a2 * dx2);
+    d.b_coef = 1.0 / (e2a2 * dx2 * dx2);
+    d.g_div = 1.0 / (em * em);
+    d.g_phi = 2.0 * dx2 * am * am;
+    d.sigma2 = c.sigma * c.sigma;
+    return d;
+}
+
+size_t padded(size_t n) { return (n + 63) & ~(size_t)63; }   // 256 B for floats
+
+}  // namespace
+
+struct ah_sim {
+    ah_config cfg;
+    int N;
+    long long nsites;
+    int64_t step;
+    int cur;
+    int device;
+    int num_sms;
+    void *dmem;
+    size_t dbytes;
+    Fields<float> f32;
+    Fields<double> f64;
+    DiagPartial *partials;
+    DiagPartial *result;
+    DiagPartial *host_result;
+    int diag_blocks;
+    cudaStream_t stream;
+    bool own_stream;
+};
+
+namespace {
+
+template <typename real>
+void carve(Fields<real> &F, char *base, size_t n)
+{
+    real *p = (real *)base;
+    const size_t pn = padded(n);
+    for (int b = 0; b < 2; ++b) {
+        F.phr[b] = p; p += pn;
+        F.phi[b] = p; p += pn;
+        for (int d = 0; d < 3; ++d) { F.th[b][d] = p; p += pn; }
+    }
+    F.pir = p; p += pn;
+    F.pii = p; p += pn;
+    for (int d = 0; d < 3; ++d) { F.el[d] = p; p += pn; }
+}
+
+template <typename real>
+View<real> make_view(const Fields<real> &F, int cur, bool pingpong)
+{
+    const int o = pingpong ? 1 - cur : cur;
+    View<real> v;
+    v.phr = F.phr[cur]; v.phi = F.phi[cur];
+    v.th1 = F.th[cur][0]; v.th2 = F.th[cur][1]; v.th3 = F.th[cur][2];
+    v.pir = F.pir; v.pii = F.pii;
+    v.e1 = F.el[0]; v.e2 = F.el[1]; v.e3 = F.el[2];
+    v.ophr = F.phr[o]; v.ophi = F.phi[o];
+    v.oth1 = F.th[o][0]; v.oth2 = F.th[o][1]; v.oth3 = F.th[o][2];
+    return v;
+}
+
+ah_status validate(const ah_config &c)
+{
+    if (c.N < 4 || c.N > 2048) return fail(AH_ERR_ARG, "N=%d outside [4, 2048]", c.N);
+    if (!(c.dx > 0) || !(c.dt > 0)) return fail(AH_ERR_ARG, "dx and dt must be > 0");
+    if (!(c.e0 > 0) || !(c.lambda0 >= 0) || !(c.sigma > 0))
+        return fail(AH_ERR_ARG, "need e0 > 0, lambda0 >= 0, sigma > 0");
+    if (c.era < AH_MINKOWSKI || c.era > AH_MATTER) return fail(AH_ERR_ARG, "unknown era %d", c.era);
+    if (c.precision != AH_FP32 && c.precision != AH_FP64)
+        return fail(AH_ERR_ARG, "unknown precision %d", c.precision);
+    if (c.kernel < AH_KERNEL_AUTO || c.kernel > AH_KERNEL_FUSED)
+        return fail(AH_ERR_ARG, "unknown kernel %d", c.kernel);
+    if (c.flags != 0) return fail(AH_ERR_ARG, "flags must be 0");
+    if (!std::isfinite(c.s)) return fail(AH_ERR_ARG, "s must be finite");
+    if (c.era != AH_MINKOWSKI && !(c.tau0 > 0)) return fail(AH_ERR_ARG, "tau0 must be > 0");
+    if (!(c.tau_ref > 0)) return fail(AH_ERR_ARG, "tau_ref must be > 0");
+    if (!(c.tau_end >= c.tau0)) return fail(AH_ERR_ARG, "tau_end must be >= tau0");
+    if (c.dt * std::sqrt(3.0) > c.dx) return fail(AH_ERR_ARG, "Courant: need dt <= dx/sqrt(3)");
+    // Leapfrog stability of the stiffest mode: lattice gradient (12/dx^2) plus the
+    // scalar / vector mass terms lambda0 sigma^2 a^2s and 2 e0^2 sigma^2 a^2s, with
+    // a^s largest at one end of [tau0, tau_end].  Require dt^2 w^2 < 0.9 * 4.
+    const double a0 = scale_factor(c, c.tau0), a1 = scale_factor(c, c.tau_end);
+    const double as2 = std::fmax(std::pow(a0, 2.0 * c.s), std::pow(a1, 2.0 * c.s));
+    const double m2 = std::fmax(c.lambda0, 2.0 * c.e0 * c.e0) * c.sigma * c.sigma * as2;
+    const double w2dt2 = c.dt * c.dt * (12.0 / (c.dx * c.dx) + m2);
+    if (!(w2dt2 < 3.6))
+        return fail(AH_ERR_UNSTABLE, "leapfrog unstable: dt^2 w_max^2 = %.3g >= 3.6 (a^s up to %.3g)",
+                    w2dt2, std::sqrt(as2));
+    return AH_OK;
+}
+
+template <typename real>
+ah_status do_step(ah_sim *h, int64_t n)
+{
+    Fields<real> &F = *(Fields<real> *)(h->cfg.precision == AH_FP32 ? (void *)&h->f32 : (void *)&h->f64);
+    const KickCoef<real> k = kick_coef<real>(h->cfg, n);
+    if (h->cfg.kernel == AH_KERNEL_PLAIN) {
+        AH_CUDA(launch_plain_step<real>(make_view(F, h->cur, false), h->N, k, h->stream));
+    } else {
+        AH_CUDA(launch_fused_step<real>(make_view(F, h->cur, true), h->N, k, h->stream));
+        h->cur ^= 1;
+    }
+    return AH_OK;
+}
+
+template <typename real>
+ah_status do_diag(ah_sim *h, Box b, ah_obs *out)
+{
+    Fields<real> &F = *(Fields<real> *)(h->cfg.precision == AH_FP32 ? (void *)&h->f32 : (void *)&h->f64);
+    const DiagCoef dc = diag_coef(h->cfg, h->step);
+    AH_CUDA(launch_diag<real>(make_view(F, h->cur, false), h->N, b, dc, h->partials, h->diag_blocks,
+                              h->result, h->stream));
+    AH_CUDA(cudaMemcpyAsync(h->host_result, h->result, sizeof(DiagPartial), cudaMemcpyDeviceToHost,
+                            h->stream));
+    AH_CUDA(cudaStreamSynchronize(h->stream));
+    const DiagPartial &r = *h->host_result;
+    const ah_config &c = h->cfg;
+    ah_obs o;
+    memset(&o, 0, sizeof o);
+    o.step = h->step;
+    o.tau = tau_of(c, h->step);
+    o.a = scale_factor(c, o.tau);
+    o.n_sites = (int64_t)b.nx * b.ny * b.nz;
+    for (int k = 0; k < kNumSums; ++k) o.sums[k] = r.sums[k];
+    for (int q = 0; q < 3; ++q) {
+        o.wind_abs_plane[q] = r.ints[q];
+        o.wind_plane[q] = r.ints[3 + q];
+    }
+    o.n_pierced = r.ints[6];
+    o.nonfinite = r.ints[7];
+    o.sum_abs_W = o.wind_abs_plane[0] + o.wind_abs_plane[1] + o.wind_abs_plane[2];
+    const double ns = (double)o.n_sites;
+    o.L_mean = o.sums[0] / ns;
+    o.xi_L = std::sqrt(-2.0 * M_PI * c.sigma * c.sigma / o.L_mean);
+    o.xi_W = std::sqrt(ns * c.dx * c.dx * c.dx / (M_PI / 6.0 * c.dx * (double)o.sum_abs_W));
+    o.R_V = o.sums[8] / o.sums[9];
+    o.R_L = o.sums[10] / o.sums[11];
+    o.v2_V = 2.0 * o.R_V / (1.0 + o.R_V);
+    o.v2_L = 2.0 * o.R_L / (1.0 + o.R_L);
+    o.p_over_rho_L = o.sums[12] / o.sums[13];
+    o.v2_omega = 0.5 * (1.0 + 3.0 * o.p_over_rho_L);
+    o.gauss_rms = std::sqrt(o.sums[14] / ns);
+    o.gauss_max = r.maxv[0];
+    o.gauss_rel = std::sqrt(o.sums[14] / o.sums[15]);
+    o.energy = c.dx * c.dx * c.dx * o.sums[1];
+    o.max_abs_theta = r.maxv[1];
+    *out = o;
+    if (o.nonfinite) return fail(AH_ERR_NONFINITE, "%lld sites have non-finite diagnostics", (long long)o.nonfinite);
+    return AH_OK;
+}
+
+ah_status enter(const ah_sim *h)
+{
+    if (!h) return fail(AH_ERR_ARG, "null simulation handle");
+    AH_CUDA(cudaSetDevice(h->device));
+    return AH_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int ah_abi_version(void) { return 1; }
+
+const char *ah_last_error(void) { return g_err.c_str(); }
+
+void ah_config_default(ah_config *c, int32_t N)
+{
+    if (!c) return;
+    memset(c, 0, sizeof *c);
+    c->N = N;
+    c->era = AH_RADIATION;
+    c->precision = AH_FP32;
+    c->kernel = AH_KERNEL_AUTO;
+    c->dx = 0.5;
+    c->dt = 0.1;
+    c->s = 0.0;
+    c->lambda0 = 2.0;
+    c->e0 = 1.0;
+    c->sigma = 1.0;
+    c->tau0 = 1.0;
+    c->tau_end = N * c->dx / 2.0;
+    c->tau_ref = c->tau_end;
+    c->seed = 1;
+}
+
+ah_status ah_create_ex(const ah_config *cfg, ah_sim **out)
+{
+    if (!cfg || !out) return fail(AH_ERR_ARG, "null argument");
+    *out = nullptr;
+    ah_status st = validate(*cfg);
+    if (st != AH_OK) return st;
+    ah_sim *h = new (std::nothrow) ah_sim();
+    if (!h) return fail(AH_ERR_OOM, "host allocation failed");
+    h->cfg = *cfg;
+    if (h->cfg.kernel == AH_KERNEL_AUTO) h->cfg.kernel = AH_KERNEL_FUSED;
+    h->N = cfg->N;
+    h->nsites = (long long)cfg->N * cfg->N * cfg->N;
+    h->step = 0;
+    h->cur = 0;
+    cudaError_t e = cudaGetDevice(&h->device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+        delete h;
+        return fail(AH_ERR_CUDA, "CUDA device setup failed: %s", cudaGetErrorString(e));
+    }
+    h->own_stream = true;
+    const size_t esz = cfg->precision == AH_FP32 ? sizeof(float) : sizeof(double);
+    h->dbytes = 15 * padded((size_t)h->nsites) * esz;
+    h->diag_blocks = diag_grid_blocks(h->num_sms);
+    e = cudaMalloc(&h->dmem, h->dbytes);
+    if (e == cudaSuccess) e = cudaMalloc((void **)&h->partials, sizeof(DiagPartial) * (h->diag_blocks + 1));
+    if (e == cudaSuccess) e = cudaMallocHost((void **)&h->host_result, sizeof(DiagPartial));
+    if (e != cudaSuccess) {
+        ah_destroy(h);
+        return fail(AH_ERR_OOM, "allocation of %.3g GB failed: %s", h->dbytes / 1e9, cudaGetErrorString(e));
+    }
+    h->result = h->partials + h->diag_blocks;
+    e = cudaMemsetAsync(h->dmem, 0, h->dbytes, h->stream);
+    if (e == cudaSuccess) {
+        if (cfg->precision == AH_FP32) {
+            carve(h->f32, (char *)h->dmem, (size_t)h->nsites);
+            e = launch_init_phase<float>(h->f32.phr[0], h->f32.phi[0], h->N, cfg->seed, cfg->sigma, h->stream);
+        } else {
+            carve(h->f64, (char *)h->dmem, (size_t)h->nsites);
+            e = launch_init_phase<double>(h->f64.phr[0], h->f64.phi[0], h->N, cfg->seed, cfg->sigma, h->stream);
+        }
+    }
+    if (e != cudaSuccess) {
+        ah_destroy(h);
+        return fail(AH_ERR_CUDA, "initialisation failed: %s", cudaGetErrorString(e));
+    }
+    *out = h;
+    return AH_OK;
+}
+
+ah_sim *ah_create(int32_t N, double dx, double dt, int32_t era, double s, double lambda0, double e0,
+                  uint64_t seed)
+{
+    ah_config c;
+    ah_config_default(&c, N);
+    c.dx = dx;
+    c.dt = dt;
+    c.era = era;
+    c.s = s;
+    c.lambda0 = lambda0;
+    c.e0 = e0;
+    c.seed = seed;
+    c.tau_end = N * dx / 2.0;
+    c.tau_ref = c.tau_end;
+    ah_sim *h = nullptr;
+    return ah_create_ex(&c, &h) == AH_OK ? h : nullptr;
+}
+
+ah_status ah_step(ah_sim *h, int64_t nsteps)
+{
+    ah_status st = enter(h);
+    if (st != AH_OK) return st;
+    if (nsteps < 0) return fail(AH_ERR_ARG, "nsteps must be >= 0");
+    for (int64_t q = 0; q < nsteps; ++q) {
+        st = h->cfg.precision == AH_FP32 ? do_step<float>(h, h->step) : do_step<double>(h, h->step);
+        if (st != AH_OK) return st;
+        ++h->step;
+    }
+    return AH_OK;
+}
+
+ah_status ah_observables_box(ah_sim *h, int32_t x0, int32_t y0, int32_t z0, int32_t nx, int32_t ny,
+                             int32_t nz, ah_obs *out)
+{
+    ah_status st = enter(h);
+    if (st != AH_OK) return st;
+    if (!out) return fail(AH_ERR_ARG, "null output");
+    const int N = h->N;
+    if (nx < 1 || ny < 1 || nz < 1 || nx > N || ny > N || nz > N)
+        return fail(AH_ERR_ARG, "box extent must be in [1, N]");
+    auto md = [N](int v) { v %= N; return v < 0 ? v + N : v; };
+    const Box b{ md(x0), md(y0), md(z0), nx, ny, nz };
+    return h->cfg.precision == AH_FP32 ? do_diag<float>(h, b, out) : do_diag<double>(h, b, out);
+}
+
+ah_status ah_observables(ah_sim *h, ah_obs *out)
+{
+    if (!h) return fail(AH_ERR_ARG, "null simulation handle");
+    return ah_observables_box(h, 0, 0, 0, h->N, h->N, h->N, out);
+}
+
+ah_status ah_get_fields(ah_sim *h, int32_t x0, int32_t y0, int32_t z0, int32_t nx, int32_t ny, int32_t nz,
+                        double *out)
+{
+    ah_status st = enter(h);
+    if (st != AH_OK) return st;
+    if (!out) return fail(AH_ERR_ARG, "null output");
+    const int N = h->N;
+    if (nx < 1 || ny < 1 || nz < 1 || nx > N || ny > N || nz > N)
+        return fail(AH_ERR_ARG, "window extent must be in [1, N]");
+    auto md = [N](int v) { v %= N; return v < 0 ? v + N : v; };
+    const Box b{ md(x0), md(y0), md(z0), nx, ny, nz };
+    const size_t bytes = sizeof(double) * 10 * (size_t)nx * ny * nz;
+    double *tmp = nullptr;
+    AH_CUDA(cudaMalloc(&tmp, bytes));
+    cudaError_t e = h->cfg.precision == AH_FP32
+                        ? launch_gather_window<float>(h->f32, h->cur, N, b, tmp, h->stream)
+                        : launch_gather_window<double>(h->f64, h->cur, N, b, tmp, h->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(out, tmp, bytes, cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    cudaFree(tmp);
+    if (e != cudaSuccess) return fail(AH_ERR_CUDA, "get_fields failed: %s", cudaGetErrorString(e));
+    return AH_OK;
+}
+
+ah_status ah_set_fields(ah_sim *h, const double *in, int64_t step)
+{
+    ah_status st = enter(h);
+    if (st != AH_OK) return st;
+    if (!in || step < 0) return fail(AH_ERR_ARG, "null input or negative step");
+    const size_t bytes = sizeof(double) * 10 * (size_t)h->nsites;
+    double *tmp = nullptr;
+    AH_CUDA(cudaMalloc(&tmp, bytes));
+    cudaError_t e = cudaMemcpyAsync(tmp, in, bytes, cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess)
+        e = h->cfg.precision == AH_FP32 ? launch_scatter_all<float>(h->f32, h->cur, h->N, tmp, h->stream)
+                                        : launch_scatter_all<double>(h->f64, h->cur, h->N, tmp, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    cudaFree(tmp);
+    if (e != cudaSuccess) return fail(AH_ERR_CUDA, "set_fields failed: %s", cudaGetErrorString(e));
+    h->step = step;
+    return AH_OK;
+}
+
+ah_status ah_set_stream(ah_sim *h, void *stream)
+{
+    ah_status st = enter(h);
+    if (st != AH_OK) return st;
+    AH_CUDA(cudaStreamSynchronize(h->stream));
+    if (stream) {
+        if (h->own_stream) cudaStreamDestroy(h->stream);
+        h->stream = (cudaStream_t)stream;
+        h->own_stream = false;
+    } else if (!h->own_stream) {
+        AH_CUDA(cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking));
+        h->own_stream = true;
+    }
+    return AH_OK;
+}
+
+ah_status ah_sync(ah_sim *h)
+{
+    ah_status st = enter(h);
+    if (st != AH_OK) return st;
+    AH_CUDA(cudaStreamSynchronize(h->stream));
+    return AH_OK;
+}
+
+int64_t ah_get_step(const ah_sim *h) { return h ? h->step : -1; }
+
+double ah_get_tau(const ah_sim *h) { return h ? tau_of(h->cfg, h->step) : NAN; }
+
+ah_status ah_get_info(const ah_sim *h, ah_info *out)
+{
+    if (!h || !out) return fail(AH_ERR_ARG, "null argument");
+    const int64_t esz = h->cfg.precision == AH_FP32 ? 4 : 8;
+    out->N = h->N;
+    out->n_sites = h->nsites;
+    out->precision = h->cfg.precision;
+    out->kernel = h->cfg.kernel;
+    out->state_bytes = (int64_t)h->dbytes;
+    out->step_bytes = 20 * esz * h->nsites;
+    out->step_launches = h->cfg.kernel == AH_KERNEL_PLAIN ? 3 : 1;
+    return AH_OK;
+}
+
+void ah_destroy(ah_sim *h)
+{
+    if (!h) return;
+    cudaSetDevice(h->device);
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    if (h->dmem) cudaFree(h->dmem);
+    if (h->partials) cudaFree(h->partials);
+    if (h->host_result) cudaFreeHost(h->host_result);
+    if (h->stream && h->own_stream) cudaStreamDestroy(h->stream);
+    delete h;
+}
+
+}  // extern "C"

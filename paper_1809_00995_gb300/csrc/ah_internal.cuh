@@ -1,0 +1,92 @@
+// ah_internal.cuh -- types and kernel launchers shared by the CUDA sources of
+// the library (not part of the public ABI; see include/ah.h).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace ah {
+
+// Device pointers of one state: 10 SoA arrays of N^3 reals (x fastest).
+// phi and theta have two buffers each (ping-pong for the fused step);
+// `cur` selects the buffer holding phi^n, theta^n.
+template <typename real>
+struct Fields {
+    real *phr[2], *phi[2];
+    real *th[2][3];
+    real *pir, *pii;
+    real *el[3];
+};
+
+// View of one state for a kernel: the buffers it reads (and, for the fused
+// step, the phi/theta buffers it writes).
+template <typename real>
+struct View {
+    const real *phr, *phi, *th1, *th2, *th3;   // phi^n, theta^n
+    real *pir, *pii, *e1, *e2, *e3;              // Pi, E (updated in place)
+    real *ophr, *ophi, *oth1, *oth2, *oth3;      // phi^{n+1}, theta^{n+1}
+};
+
+// Coefficients of one leapfrog step n (Eqs. up_pi and up_E), computed in FP64
+// on the host from tau_n, tau_n +- dt/2:
+//   Pi+ = c_damp Pi- - c_pot (|phi|^2 - sigma^2) phi + c_lap * Laplacian
+//   E+  = c_edamp E-  + c_cur * current - c_curl * curl
+template <typename real>
+struct KickCoef {
+    real c_damp, c_pot, c_lap, c_edamp, c_cur, c_curl, dt, sigma2;
+};
+
+// Per-site diagnostic coefficients at step n (FP64 always).
+struct DiagCoef {
+    double inv_dx2;    // 1 / dx^2
+    double v_coef;     // a^2 lambda / 4
+    double eel_coef;   // 1 / (2 e^2 a^2 dx^2)
+    double b_coef;     // 1 / (e^2 a^2 dx^4)
+    double g_div;      // 1 / e_-^2
+    double g_phi;      // 2 dx^2 a_-^2
+    double sigma2;
+};
+
+// Number of FP64 sums and integer counters produced by the diagnostics.
+constexpr int kNumSums = 16;     // see ah_obs.sums
+constexpr int kNumMax = 2;       // max |G|, max |theta|
+constexpr int kNumInt = 8;       // |W| by plane (3), W by plane (3), pierced, nonfinite
+
+// One block's partial results of the diagnostics reduction.
+struct DiagPartial {
+    double sums[kNumSums];
+    double maxv[kNumMax];
+    long long ints[kNumInt];
+};
+
+struct Box { int x0, y0, z0, nx, ny, nz; };
+
+// ---- launchers (each returns the launch's cudaError_t) ----
+template <typename real>
+cudaError_t launch_init_phase(real *phr, real *phi, int N, uint64_t seed, double sigma,
+                              cudaStream_t st);
+
+template <typename real>
+cudaError_t launch_gather_window(const Fields<real> &F, int cur, int N, Box b, double *out,
+                                 cudaStream_t st);
+
+template <typename real>
+cudaError_t launch_scatter_all(const Fields<real> &F, int cur, int N, const double *in,
+                               cudaStream_t st);
+
+template <typename real>
+cudaError_t launch_plain_step(const View<real> &v, int N, const KickCoef<real> &c,
+                              cudaStream_t st);
+
+template <typename real>
+cudaError_t launch_fused_step(const View<real> &v, int N, const KickCoef<real> &c,
+                              cudaStream_t st);
+
+template <typename real>
+cudaError_t launch_diag(const View<real> &v, int N, Box b, const DiagCoef &c,
+                        DiagPartial *partials, int nblocks, DiagPartial *result,
+                        cudaStream_t st);
+
+int diag_grid_blocks(int num_sms);
+
+}  // namespace ah

@@ -1,0 +1,293 @@
+// k_fused.cu -- fused leapfrog step: both kicks and both drifts of one time
+// step (Eqs. up_pi, up_E, up_phi, up_A of arXiv:1809.00995) in one z-marching
+// kernel.
+//
+// A CTA owns a TX x TY column of sites in the XY plane and a chunk of z planes.
+// For each plane z it keeps, in shared memory, the link exponentials
+// U_d = e^{i theta_d} and phi of planes z and z+1 on the tile plus a one-site
+// halo ring, and the plaquette sines sin Xi_ij = Im(U_i U_j^{x+i} conj(U_i^{x+j})
+// conj(U_j)) of plane z on the tile plus its low halos.  Each link exponential is
+// computed once per site and shared by the covariant Laplacian, the scalar
+// current and the three plaquettes; each plaquette sine is computed once and
+// shared by the four E kicks that use it.  Values of plane z-1 that a site
+// needs (phi, U_3, sin Xi_13, sin Xi_23) stay in the owning thread's registers
+// as the CTA marches up in z, and the next plane's fields are prefetched into
+// registers one plane ahead.
+//
+// phi and theta are read from one buffer and written to the other (ping-pong),
+// Pi and E are updated in place, so every step reads and writes the 10-real
+// state exactly once from DRAM; halo re-reads are served by L2.  Periodic
+// boundaries are applied in the index arithmetic.
+#include "ah_internal.cuh"
+
+namespace ah {
+namespace {
+
+template <typename real>
+struct cpx { real r, i; };
+
+__device__ __forceinline__ void sc(float t, float *s, float *c) { sincosf(t, s, c); }
+__device__ __forceinline__ void sc(double t, double *s, double *c) { sincos(t, s, c); }
+
+template <typename real>
+__device__ __forceinline__ cpx<real> mul(cpx<real> a, cpx<real> b)
+{
+    return { a.r * b.r - a.i * b.i, a.r * b.i + a.i * b.r };
+}
+// Im(a b conj(c) conj(d)) = Im((a b) conj(c d))
+template <typename real>
+__device__ __forceinline__ real plaq(cpx<real> a, cpx<real> b, cpx<real> c, cpx<real> d)
+{
+    const cpx<real> ab = mul(a, b), cd = mul(c, d);
+    return ab.i * cd.r - ab.r * cd.i;
+}
+
+__device__ __forceinline__ int wrapm(int a, int N)
+{
+    a %= N;
+    return a < 0 ? a + N : a;
+}
+
+template <typename real, int TY>
+struct Geo {
+    static constexpr int TX = 32, NT = 256, RY = TY / 8;
+    static constexpr int EX = TX + 2, EY = TY + 2, NE = EX * EY;
+    static constexpr int NHALO = 2 * EX + 2 * TY;
+    static constexpr int PX = TX + 1, PY = TY + 1, NP = PX * PY;
+    static constexpr int NPHALO = PX + TY;
+    static constexpr size_t smem = sizeof(cpx<real>) * (2 * 3 * NE + 2 * NE) + sizeof(real) * 3 * NP;
+    static_assert(TY % 8 == 0 && NHALO <= NT && NPHALO <= NT, "tile shape");
+};
+
+template <typename real, int TY>
+__global__ void __launch_bounds__(256) k_fused(View<real> v, int N, int zc, KickCoef<real> c)
+{
+    using G = Geo<real, TY>;
+    constexpr int TX = G::TX, RY = G::RY, EX = G::EX, EY = G::EY, NE = G::NE, PX = G::PX;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    cpx<real> *sU = reinterpret_cast<cpx<real> *>(smem_raw);   // [2 planes][3 dirs][NE]
+    cpx<real> *sF = sU + 2 * 3 * NE;                            // [2 planes][NE] phi
+    real *sP = reinterpret_cast<real *>(sF + 2 * NE);           // [3][NP] sin Xi_12, _13, _23
+
+    const int tid = threadIdx.x, lx = tid & 31, wy = tid >> 5;
+    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+    const int z0 = blockIdx.z * zc;
+    if (z0 >= N) return;
+    const int z1 = min(z0 + zc, N);
+    const long long NN = (long long)N * N;
+
+    // In-plane offsets and extended-tile slots of this thread's tasks: its RY own
+    // sites, then (for tid < NHALO) one site of the halo ring.
+    int off[RY + 1], eix[RY + 1];
+    bool wr[RY];
+#pragma unroll
+    for (int m = 0; m < RY; ++m) {
+        const int gx = x0 + lx, gy = y0 + wy + 8 * m;
+        wr[m] = gx < N && gy < N;
+        off[m] = wrapm(gx, N) + N * wrapm(gy, N);
+        eix[m] = (wy + 8 * m + 1) * EX + lx + 1;
+    }
+    const bool has_halo = tid < G::NHALO;
+    {
+        int ex = 0, ey = 0;
+        const int h = tid;
+        if (h < EX) { ex = h; ey = 0; }
+        else if (h < 2 * EX) { ex = h - EX; ey = EY - 1; }
+        else if (h < 2 * EX + TY) { ex = 0; ey = 1 + h - 2 * EX; }
+        else { ex = EX - 1; ey = 1 + h - 2 * EX - TY; }
+        off[RY] = wrapm(x0 + ex - 1, N) + N * wrapm(y0 + ey - 1, N);
+        eix[RY] = ey * EX + ex;
+    }
+
+    // register prefetch of one plane's phi, theta for every task
+    real fth[RY + 1][3], fph[RY + 1][2];
+    auto load_plane = [&](int z) {
+        const long long base = (long long)wrapm(z, N) * NN;
+#pragma unroll
+        for (int t = 0; t <= RY; ++t) {
+            if (t < RY || has_halo) {
+                const long long s = base + off[t];
+                fth[t][0] = v.th1[s]; fth[t][1] = v.th2[s]; fth[t][2] = v.th3[s];
+                fph[t][0] = v.phr[s]; fph[t][1] = v.phi[s];
+            }
+        }
+    };
+    // U and phi of the prefetched plane into shared buffer b
+    auto store_plane = [&](int b) {
+#pragma unroll
+        for (int t = 0; t <= RY; ++t) {
+            if (t < RY || has_halo) {
+#pragma unroll
+                for (int d = 0; d < 3; ++d) {
+                    real s, co;
+                    sc(fth[t][d], &s, &co);
+                    sU[(b * 3 + d) * NE + eix[t]] = { co, s };
+                }
+                sF[b * NE + eix[t]] = { fph[t][0], fph[t][1] };
+            }
+        }
+    };
+
+    // own-site registers carried along z
+    cpx<real> ph_m[RY], ph_0[RY], u3_m[RY];
+    real th_0[RY][3], p13_m[RY], p23_m[RY];
+
+    // prologue: planes z0-1 and z0
+    load_plane(z0 - 1);
+    const int bm = (z0 - 1) & 1, b0 = z0 & 1;
+    store_plane(bm);
+#pragma unroll
+    for (int m = 0; m < RY; ++m) ph_m[m] = { fph[m][0], fph[m][1] };
+    load_plane(z0);
+    store_plane(b0);
+#pragma unroll
+    for (int m = 0; m < RY; ++m) {
+        ph_0[m] = { fph[m][0], fph[m][1] };
+        th_0[m][0] = fth[m][0]; th_0[m][1] = fth[m][1]; th_0[m][2] = fth[m][2];
+    }
+    load_plane(z0 + 1);
+    __syncthreads();
+#pragma unroll
+    for (int m = 0; m < RY; ++m) {
+        const int e = eix[m];
+        const cpx<real> *Um = sU + bm * 3 * NE, *U0 = sU + b0 * 3 * NE;
+        u3_m[m] = Um[2 * NE + e];
+        p13_m[m] = plaq(Um[e], Um[2 * NE + e + 1], U0[e], Um[2 * NE + e]);
+        p23_m[m] = plaq(Um[NE + e], Um[2 * NE + e + EX], U0[NE + e], Um[2 * NE + e]);
+    }
+    __syncthreads();
+
+    for (int z = z0; z < z1; ++z) {
+        const int bc = z & 1, bn = (z + 1) & 1;
+        const long long base = (long long)z * NN;
+        // Pi, E of plane z (consumed after two barriers)
+        real pr[RY], pim[RY], e1[RY], e2[RY], e3[RY];
+#pragma unroll
+        for (int m = 0; m < RY; ++m) {
+            const long long s = base + off[m];
+            pr[m] = v.pir[s]; pim[m] = v.pii[s];
+            e1[m] = v.e1[s]; e2[m] = v.e2[s]; e3[m] = v.e3[s];
+        }
+        // A: links and phi of plane z+1 from the prefetch, then prefetch z+2
+        store_plane(bn);
+        cpx<real> ph_p[RY];
+        real th_p[RY][3];
+#pragma unroll
+        for (int m = 0; m < RY; ++m) {
+            ph_p[m] = { fph[m][0], fph[m][1] };
+            th_p[m][0] = fth[m][0]; th_p[m][1] = fth[m][1]; th_p[m][2] = fth[m][2];
+        }
+        load_plane(z + 2);
+        __syncthreads();
+
+        // B: plaquette sines of plane z on the tile (own sites) and its low halos
+        const cpx<real> *U0 = sU + bc * 3 * NE, *U1p = sU + bn * 3 * NE;
+        real p12[RY], p13[RY], p23[RY];
+#pragma unroll
+        for (int m = 0; m < RY; ++m) {
+            const int e = eix[m];
+            p12[m] = plaq(U0[e], U0[NE + e + 1], U0[e + EX], U0[NE + e]);
+            p13[m] = plaq(U0[e], U0[2 * NE + e + 1], U1p[e], U0[2 * NE + e]);
+            p23[m] = plaq(U0[NE + e], U0[2 * NE + e + EX], U1p[NE + e], U0[2 * NE + e]);
+            const int p = (wy + 8 * m + 1) * PX + lx + 1;
+            sP[p] = p12[m];
+            sP[G::NP + p] = p13[m];
+            sP[2 * G::NP + p] = p23[m];
+        }
+        if (tid < G::NPHALO) {
+            const int px = tid < PX ? tid : 0, py = tid < PX ? 0 : tid - PX + 1;
+            const int e = py * EX + px, p = py * PX + px;
+            sP[p] = plaq(U0[e], U0[NE + e + 1], U0[e + EX], U0[NE + e]);
+            sP[G::NP + p] = plaq(U0[e], U0[2 * NE + e + 1], U1p[e], U0[2 * NE + e]);
+            sP[2 * G::NP + p] = plaq(U0[NE + e], U0[2 * NE + e + EX], U1p[NE + e], U0[2 * NE + e]);
+        }
+        __syncthreads();
+
+        // C: kicks and drifts of the own sites of plane z
+        const cpx<real> *F0 = sF + bc * NE;
+#pragma unroll
+        for (int m = 0; m < RY; ++m) {
+            const int e = eix[m];
+            const int p = (wy + 8 * m + 1) * PX + lx + 1;
+            const cpx<real> f0 = ph_0[m];
+            const cpx<real> u1 = U0[e], u2 = U0[NE + e], u3 = U0[2 * NE + e];
+            const cpx<real> u1m = U0[e - 1], u2m = U0[NE + e - EX], u3m = u3_m[m];
+            // forward products U_d phi^{x+d}; backward conj(U_d^{x-d}) phi^{x-d}
+            const cpx<real> w1 = mul(u1, F0[e + 1]), w2 = mul(u2, F0[e + EX]), w3 = mul(u3, ph_p[m]);
+            const cpx<real> b1 = mul({ u1m.r, -u1m.i }, F0[e - 1]);
+            const cpx<real> b2 = mul({ u2m.r, -u2m.i }, F0[e - EX]);
+            const cpx<real> b3 = mul({ u3m.r, -u3m.i }, ph_m[m]);
+            const real lr = (w1.r + b1.r) + (w2.r + b2.r) + (w3.r + b3.r) - real(6) * f0.r;
+            const real li = (w1.i + b1.i) + (w2.i + b2.i) + (w3.i + b3.i) - real(6) * f0.i;
+            const real pot = c.c_pot * (f0.r * f0.r + f0.i * f0.i - c.sigma2);
+            const real npr = c.c_damp * pr[m] - pot * f0.r + c.c_lap * lr;
+            const real npi = c.c_damp * pim[m] - pot * f0.i + c.c_lap * li;
+            // current Im[conj(U_i phi^{x+i}) phi^x]
+            const real cu1 = w1.r * f0.i - w1.i * f0.r;
+            const real cu2 = w2.r * f0.i - w2.i * f0.r;
+            const real cu3 = w3.r * f0.i - w3.i * f0.r;
+            // curls sum_{j != i} [sin Xi_ij^x - sin Xi_ij^{x-j}], Xi_ji = -Xi_ij
+            const real q12 = p12[m], q13 = p13[m], q23 = p23[m];
+            const real cl1 = (q12 - sP[p - PX]) + (q13 - p13_m[m]);
+            const real cl2 = (sP[p - 1] - q12) + (q23 - p23_m[m]);
+            const real cl3 = (sP[G::NP + p - 1] - q13) + (sP[2 * G::NP + p - PX] - q23);
+            const real ne1 = c.c_edamp * e1[m] + c.c_cur * cu1 - c.c_curl * cl1;
+            const real ne2 = c.c_edamp * e2[m] + c.c_cur * cu2 - c.c_curl * cl2;
+            const real ne3 = c.c_edamp * e3[m] + c.c_cur * cu3 - c.c_curl * cl3;
+            if (wr[m]) {
+                const long long s = base + off[m];
+                v.pir[s] = npr; v.pii[s] = npi;
+                v.e1[s] = ne1; v.e2[s] = ne2; v.e3[s] = ne3;
+                v.ophr[s] = f0.r + c.dt * npr;
+                v.ophi[s] = f0.i + c.dt * npi;
+                v.oth1[s] = th_0[m][0] + c.dt * ne1;
+                v.oth2[s] = th_0[m][1] + c.dt * ne2;
+                v.oth3[s] = th_0[m][2] + c.dt * ne3;
+            }
+            // march: plane z becomes z-1
+            ph_m[m] = f0;
+            u3_m[m] = u3;
+            p13_m[m] = q13;
+            p23_m[m] = q23;
+            ph_0[m] = ph_p[m];
+            th_0[m][0] = th_p[m][0]; th_0[m][1] = th_p[m][1]; th_0[m][2] = th_p[m][2];
+        }
+        __syncthreads();
+    }
+}
+
+template <typename real, int TY>
+cudaError_t launch_ty(const View<real> &v, int N, const KickCoef<real> &c, cudaStream_t st)
+{
+    using G = Geo<real, TY>;
+    static bool configured = false;   // per (real, TY) instantiation
+    if (!configured) {
+        cudaError_t e = cudaFuncSetAttribute(k_fused<real, TY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)G::smem);
+        if (e != cudaSuccess) return e;
+        configured = true;
+    }
+    const int tx = (N + G::TX - 1) / G::TX, ty = (N + TY - 1) / TY;
+    // enough z chunks for several waves of CTAs, chunks of at least 16 planes
+    int nch = (int)((152LL * 16 + (long long)tx * ty - 1) / ((long long)tx * ty));
+    nch = max(1, min(nch, N / 16));
+    const int zc = (N + nch - 1) / nch;
+    nch = (N + zc - 1) / zc;
+    k_fused<real, TY><<<dim3(tx, ty, nch), G::NT, G::smem, st>>>(v, N, zc, c);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+template <>
+cudaError_t launch_fused_step<float>(const View<float> &v, int N, const KickCoef<float> &c, cudaStream_t st)
+{
+    return launch_ty<float, 16>(v, N, c, st);
+}
+template <>
+cudaError_t launch_fused_step<double>(const View<double> &v, int N, const KickCoef<double> &c, cudaStream_t st)
+{
+    return launch_ty<double, 16>(v, N, c, st);
+}
+
+}  // namespace ah

@@ -1,0 +1,53 @@
+"""Host-only checks of the C ABI (no GPU needed): the library builds for
+sm_103a, loads, exports every function include/ah.h declares, and the ctypes
+structs of the binding match the C layouts."""
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+import paper_1809_00995_gb300 as ah
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "ah.h")
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(ah_[a-z_0-9]+)\s*\(", text)))
+
+
+def test_library_exports_every_declared_function():
+    lib = ah.load()
+    names = declared_functions()
+    assert "ah_create" in names and "ah_step" in names and "ah_observables" in names
+    for n in names:
+        assert hasattr(lib, n), n
+    assert set(names) <= set(ah.exported_symbols())
+    out = subprocess.run(["nm", "-D", "--defined-only", ah.lib_path()], capture_output=True, text=True).stdout
+    exported = set(re.findall(r" T (ah_\w+)", out))
+    assert set(names) <= exported
+
+
+def test_abi_version_and_struct_layouts(tmp_path):
+    assert ah.ah_abi_version() == 1
+    src = tmp_path / "sz.c"
+    src.write_text('#include "ah.h"\n#include <stdio.h>\n#include <stddef.h>\n'
+                   'int main(void){printf("%zu %zu %zu %zu %zu %zu\\n", sizeof(ah_config), sizeof(ah_obs),'
+                   ' sizeof(ah_info), offsetof(ah_obs, sums), offsetof(ah_obs, nonfinite),'
+                   ' offsetof(ah_config, seed));return 0;}\n')
+    exe = tmp_path / "sz"
+    subprocess.run(["gcc", "-I" + os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = [int(v) for v in subprocess.run([str(exe)], capture_output=True, text=True).stdout.split()]
+    want = [ctypes.sizeof(ah.ah_config), ctypes.sizeof(ah.ah_obs), ctypes.sizeof(ah.ah_info),
+            ah.ah_obs.sums.offset, ah.ah_obs.nonfinite.offset, ah.ah_config.seed.offset]
+    assert got == want
+
+
+def test_config_defaults_without_gpu():
+    c = ah.ah_config_default(64)
+    assert (c.N, c.era, c.precision, c.dx, c.dt, c.lambda0, c.e0, c.sigma) == (64, 1, 0, 0.5, 0.1, 2.0, 1.0, 1.0)
+    assert c.tau_end == 16.0 and c.tau_ref == 16.0 and c.tau0 == 1.0

@@ -1,0 +1,213 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle.
+
+Fields after 20 steps must agree per component within
+max|f_gpu - f_ref| / max(max|f_ref|, 1) <= 1e-12 (FP64 state) and 1e-5 (FP32
+state); diagnostic sums agree to FP64 rounding and winding counts exactly when
+both sides evaluate the same snapshot.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+import paper_1809_00995_gb300 as ah
+from inputs import random_state, straight_strings
+
+pytestmark = pytest.mark.gpu
+
+TOL = {ah.AH_FP64: 1e-12, ah.AH_FP32: 1e-5}
+KERNELS = [ah.AH_KERNEL_PLAIN, ah.AH_KERNEL_FUSED]
+
+
+def rel_err(got, ref):
+    """Per-component max |got - ref| / max(max |ref|, 1)."""
+    return [float(np.max(np.abs(got[c] - ref[c])) / max(np.max(np.abs(ref[c])), 1.0)) for c in range(10)]
+
+
+def oparams(N, era=ah.AH_RADIATION, s=0.0, seed=1, **kw):
+    return O.Params(N=N, era=era, s=s, seed=seed, **kw)
+
+
+def sim(N, precision, kernel, era=ah.AH_RADIATION, s=0.0, seed=1, **kw):
+    return ah.Sim(N, precision=precision, kernel=kernel, era=era, s=s, seed=seed, **kw)
+
+
+def compare_obs(go, oo, exact_windings=True):
+    S1 = abs(oo["sum_rho"])
+    S2 = S1 * S1 / oo["n_sites"]
+    names1 = ["L", "rho", "p", "K", "G2", "V", "Eel", "B"]
+    okeys = ["sum_L", "sum_rho", "sum_p", "sum_K", "sum_G2", "sum_V", "sum_Eel", "sum_B",
+             "sum_KV", "sum_G2V", "sum_KL", "sum_G2L", "sum_pL", "sum_rhoL"]
+    for k, name in enumerate(okeys):
+        ref, got = oo[name], go["sums"][k]
+        scale = S1 if k < len(names1) else S2
+        assert abs(got - ref) <= 1e-10 * max(abs(ref), 1e-6 * scale), (name, got, ref)
+    if exact_windings:
+        assert list(go["wind_abs_plane"]) == list(oo["sum_abs_W_plane"])
+        assert list(go["wind_plane"]) == list(oo["sum_W_plane"])
+        assert go["n_pierced"] == oo["n_pierced"]
+    assert go["nonfinite"] == 0 and oo["nonfinite"] == 0
+    assert abs(go["max_abs_theta"] - oo["max_abs_theta"]) <= 1e-12 * max(1.0, oo["max_abs_theta"])
+
+
+# ------------------------------------------------------------------ init
+@pytest.mark.parametrize("precision", [ah.AH_FP64, ah.AH_FP32])
+@pytest.mark.parametrize("N", [4, 7, 32])
+def test_initial_state_matches_oracle(N, precision):
+    with sim(N, precision, ah.AH_KERNEL_FUSED, seed=77) as s:
+        got = s.fields()
+    ref = O.init(oparams(N, seed=77))
+    if precision == ah.AH_FP64:
+        assert np.max(np.abs(got - ref)) < 4e-16
+    else:
+        r32 = ref.astype(np.float32).astype(np.float64)
+        d = np.abs(got - r32)
+        assert np.max(d) <= 6e-8          # at most one FP32 ulp (library sincos ulps)
+        assert np.mean(d > 0) < 0.01
+    assert not np.any(got[2:])
+
+
+# ------------------------------------------------------------------ fields after 20 steps
+CASES = [(4, ah.AH_RADIATION, 0.0), (6, ah.AH_MATTER, 1.0), (8, ah.AH_MINKOWSKI, 0.0),
+         (33, ah.AH_RADIATION, 0.0), (40, ah.AH_MATTER, 1.0), (17, ah.AH_RADIATION, -0.5)]
+
+
+@pytest.mark.parametrize("kernel", KERNELS)
+@pytest.mark.parametrize("precision", [ah.AH_FP64, ah.AH_FP32])
+@pytest.mark.parametrize("N,era,s", CASES)
+def test_fields_after_20_steps(N, era, s, precision, kernel):
+    p = oparams(N, era, s, seed=N + 3)
+    with sim(N, precision, kernel, era, s, seed=N + 3) as g:
+        f0 = g.fields()                         # the GPU's own initial snapshot
+        g.step(20)
+        got = g.fields()
+        assert g.n == 20
+    ref = O.evolve(p, f0.copy(), 0, 20)
+    err = rel_err(got, ref)
+    assert max(err) <= TOL[precision], err
+
+
+@pytest.mark.parametrize("kernel", KERNELS)
+@pytest.mark.parametrize("precision", [ah.AH_FP64, ah.AH_FP32])
+def test_fields_from_random_state(precision, kernel):
+    """Random phi, Pi, theta, E: every term of both kicks active from the first step."""
+    N = 24
+    p = oparams(N, ah.AH_MATTER, 0.5, tau_ref=9.0)
+    f = random_state(N, 5)
+    with sim(N, precision, kernel, ah.AH_MATTER, 0.5, tau_ref=9.0) as g:
+        g.set_fields(f, step=3)
+        f0 = g.fields()
+        g.step(20)
+        got = g.fields()
+    ref = O.evolve(p, f0.copy(), 3, 20)
+    assert max(rel_err(got, ref)) <= TOL[precision]
+
+
+def test_plain_and_fused_agree_fp64():
+    with sim(32, ah.AH_FP64, ah.AH_KERNEL_PLAIN, seed=9) as a, sim(32, ah.AH_FP64, ah.AH_KERNEL_FUSED, seed=9) as b:
+        a.step(30)
+        b.step(30)
+        assert max(rel_err(a.fields(), b.fields())) < 1e-13
+
+
+# ------------------------------------------------------------------ diagnostics
+@pytest.mark.parametrize("precision", [ah.AH_FP64, ah.AH_FP32])
+@pytest.mark.parametrize("N,era,s", [(32, ah.AH_RADIATION, 0.0), (21, ah.AH_MATTER, 1.0)])
+def test_observables_match_oracle_on_same_snapshot(N, era, s, precision):
+    p = oparams(N, era, s, seed=4)
+    with sim(N, precision, ah.AH_KERNEL_FUSED, era, s, seed=4) as g:
+        for n in (0, 10, 20):
+            if n:
+                g.step(10)
+            snap = g.fields()
+            go = g.observables()
+            oo = O.observables(p, snap, n)
+            compare_obs(go, oo)
+            assert go["step"] == n and math.isclose(go["tau"], 1.0 + 0.1 * n)
+            for k in ("xi_L", "v2_V", "v2_L", "v2_omega"):
+                if math.isfinite(oo[k]):
+                    assert abs(go[k] - oo[k]) <= 1e-8 * max(1.0, abs(oo[k])), k
+            if n:
+                assert go["sum_abs_W"] > 0
+                assert abs(go["xi_W"] - oo["xi_W"]) <= 1e-12 * oo["xi_W"]
+
+
+def test_observables_box_matches_oracle_window():
+    N = 24
+    p = oparams(N, ah.AH_RADIATION, 0.0, seed=12)
+    with sim(N, ah.AH_FP64, ah.AH_KERNEL_FUSED, seed=12) as g:
+        g.step(15)
+        snap = g.fields()
+        for box in [(20, 3, 17, 9, 24, 11), (0, 0, 0, 5, 5, 5), (23, 23, 23, 1, 2, 3)]:
+            go = g.observables_box(*box)
+            oo = O.observables(p, snap, 15, box=box)
+            compare_obs(go, oo)
+            assert go["n_sites"] == box[3] * box[4] * box[5]
+
+
+@pytest.mark.parametrize("precision", [ah.AH_FP64, ah.AH_FP32])
+def test_gauss_law_preserved_on_gpu(precision):
+    tol = 1e-12 if precision == ah.AH_FP64 else 2e-4
+    with sim(48, precision, ah.AH_KERNEL_FUSED, ah.AH_MATTER, 1.0, seed=5) as g:
+        assert g.observables()["gauss_max"] == 0.0
+        g.step(100)
+        o = g.observables()
+    assert o["gauss_max"] < tol and o["sums"][3] > 1.0
+
+
+@pytest.mark.parametrize("axis", [0, 1, 2])
+def test_straight_string_windings_on_gpu(axis):
+    N = 20
+    f = straight_strings(N, axis=axis)
+    with sim(N, ah.AH_FP64, ah.AH_KERNEL_FUSED) as g:
+        g.set_fields(f)
+        o = g.observables()
+    plane = {2: 0, 1: 1, 0: 2}[axis]
+    assert o["wind_abs_plane"][plane] == 4 * N and o["wind_plane"][plane] == 0
+    assert o["sum_abs_W"] == 4 * N and o["n_pierced"] == 4 * N
+
+
+# ------------------------------------------------------------------ edge cases and checkpoint
+def test_invalid_and_unstable_configs_are_rejected():
+    with pytest.raises(ah.AhError) as e:
+        ah.Sim(3)
+    assert e.value.status == ah.AH_ERR_ARG
+    with pytest.raises(ah.AhError) as e:
+        ah.Sim(8, dt=0.4)                     # Courant
+    assert e.value.status == ah.AH_ERR_ARG
+    with pytest.raises(ah.AhError) as e:      # stiff mass term: a(tau0) = 1, s = 1, lambda0 huge
+        ah.Sim(8, lambda0=400.0, s=1.0, era=ah.AH_MATTER, tau_ref=1.0)
+    assert e.value.status == ah.AH_ERR_UNSTABLE
+    with ah.Sim(8) as g:
+        with pytest.raises(ah.AhError):
+            g.step(-1)
+        g.step(0)
+        assert g.n == 0
+        with pytest.raises(ah.AhError):
+            g.observables_box(0, 0, 0, 9, 1, 1)
+    with pytest.raises(ah.AhError):
+        ah.ah_create(3, 0.5, 0.1, 1, 0.0, 2.0, 1.0, 1)
+
+
+@pytest.mark.parametrize("precision", [ah.AH_FP64, ah.AH_FP32])
+def test_checkpoint_resume_is_bit_identical(precision):
+    with sim(20, precision, ah.AH_KERNEL_FUSED, seed=8) as a:
+        a.step(7)
+        snap = a.fields()
+        a.step(9)
+        want = a.fields()
+    with sim(20, precision, ah.AH_KERNEL_FUSED, seed=999) as b:
+        b.set_fields(snap, step=7)
+        b.step(9)
+        assert np.array_equal(b.fields(), want)
+
+
+def test_stepping_is_deterministic():
+    outs = []
+    for _ in range(2):
+        with sim(36, ah.AH_FP32, ah.AH_KERNEL_FUSED, seed=3) as g:
+            g.step(25)
+            outs.append((g.fields(), g.observables()["sums"]))
+    assert np.array_equal(outs[0][0], outs[1][0])
+    assert outs[0][1] == outs[1][1]

@@ -39,6 +39,9 @@ WORKLOADS = {
                                "256^3 FP32 state, radiation era a~tau, s=0, seed 2, diagnostics every 20 steps"),
     "lattice256_fp64_rad_s0": (256, 1, 1, 0.0, 2, 20,
                                "256^3 FP64 state, radiation era a~tau, s=0, seed 2, diagnostics every 20 steps"),
+    # profiling-sized case of the default workload (3.2 GB state, larger than L2)
+    "lattice384_fp32_matter_s1": (384, 0, 2, 1.0, 3, 50,
+                                  "384^3 FP32 state, matter era a~tau^2, s=1, seed 3, diagnostics every 50 steps"),
 }
 DEFAULT = "lattice1024_fp32_matter_s1"
 BYTES_PER_SITE = {0: 80, 1: 160}      # one read + one write of the 10-real state
@@ -141,7 +144,7 @@ def cpu_oracle_rate(wl, budget_s=12.0, M=48):
     O.evolve(p, f, 0, 1)                       # warm (threads, pages)
     n, t0 = 0, time.perf_counter()
     while True:
-        O.evolve(p, f, 1 + n, 1)
+        O.evolve(p, f, 1 + n % 200, 1)         # stays within the first 200 steps of the run
         n += 1
         if time.perf_counter() - t0 > budget_s * 0.8:
             break

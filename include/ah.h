@@ -61,6 +61,16 @@ enum { AH_FP32 = 0, AH_FP64 = 1 };
  *         ping-pong phi/theta buffers.
  *  AUTO:  FUSED. */
 enum { AH_KERNEL_AUTO = 0, AH_KERNEL_PLAIN = 1, AH_KERNEL_FUSED = 2 };
+/* Configuration flags.
+ *  EXACT_DIAG: evaluate every diagnostic per site in FP64 with arctangent
+ *  windings (slow).  By default per-site energies are evaluated in the state
+ *  precision (accumulated in FP64), the Gauss residual in FP64, and windings by
+ *  sign carries that equal the FP64 arctangent formula, with the plaquettes
+ *  near a branch cut re-evaluated in FP64. */
+enum { AH_FLAG_EXACT_DIAG = 1, AH_FLAG_AUTOTUNE = 2 };
+/* AUTOTUNE: at creation, time every compile-time shape of the fused step on
+ * the initial state (then re-initialise it) and keep the fastest; results are
+ * cached per (device, N, precision) for the life of the process. */
 
 typedef struct ah_config {
     int32_t N;            /* lattice side, 4 <= N <= 2048                         */
@@ -78,7 +88,7 @@ typedef struct ah_config {
     double tau_ref;       /* normalisation a(tau_ref) = 1 (default tau_end)         */
     uint64_t seed;        /* Philox-4x32-10 key of the random-phase initial state   */
     int32_t diag_every;   /* diagnostic cadence used by batch and serve (0: end only) */
-    int32_t flags;        /* reserved, must be 0                                   */
+    int32_t flags;        /* AH_FLAG_* bits                                        */
 } ah_config;
 
 /* Network observables at one integer step (Sec. 2).  sums[] are the raw FP64
@@ -181,9 +191,26 @@ typedef struct ah_info {
     int32_t precision, kernel;
     int64_t state_bytes;
     int64_t step_bytes;
-    int64_t step_launches;   /* kernel launches per leapfrog step */
+    int64_t step_launches;   /* kernel launches per leapfrog step          */
+    int32_t variant;         /* shape of the fused step in use             */
+    int32_t n_variants;      /* shapes available for this precision        */
+    char variant_name[32];
 } ah_info;
 ah_status ah_get_info(const ah_sim *sim, ah_info *out);
+
+/* Number of compile-time shapes (tile height, resident CTAs per SM, z-chunk
+ * length) of the fused step for the given precision. */
+int32_t ah_variant_count(int32_t precision);
+
+/* Select the fused-step shape for later steps (0 <= variant < count).  Every
+ * shape computes the same update; they differ only in speed. */
+ah_status ah_set_variant(ah_sim *sim, int32_t variant);
+
+/* Time every fused-step shape for `trial_steps` steps on the freshly created
+ * state, keep the fastest (written to *chosen if not NULL) and restore the
+ * initial state.  Only valid before the first ah_step / ah_set_fields
+ * (AH_ERR_BUSY otherwise).  Waits for the simulation's stream. */
+ah_status ah_autotune(ah_sim *sim, int32_t trial_steps, int32_t *chosen);
 
 /* Free all resources of the simulation (NULL-safe). */
 void ah_destroy(ah_sim *sim);

@@ -26,6 +26,7 @@ AH_ERR_NONFINITE, AH_ERR_TIMEOUT, AH_ERR_BUSY, AH_ERR_CANCELLED, AH_ERR_NOTFOUND
 AH_MINKOWSKI, AH_RADIATION, AH_MATTER = 0, 1, 2
 AH_FP32, AH_FP64 = 0, 1
 AH_KERNEL_AUTO, AH_KERNEL_PLAIN, AH_KERNEL_FUSED = 0, 1, 2
+AH_FLAG_EXACT_DIAG, AH_FLAG_AUTOTUNE = 1, 2
 
 SUM_NAMES = ("L", "rho", "p", "K", "G2", "V", "Eel", "B", "KV", "G2V", "KL", "G2L", "pL", "rhoL",
              "gauss2", "gscale2")
@@ -69,7 +70,8 @@ class ah_obs(ctypes.Structure):
 class ah_info(ctypes.Structure):
     _fields_ = [("N", ctypes.c_int64), ("n_sites", ctypes.c_int64), ("precision", ctypes.c_int32),
                 ("kernel", ctypes.c_int32), ("state_bytes", ctypes.c_int64), ("step_bytes", ctypes.c_int64),
-                ("step_launches", ctypes.c_int64)]
+                ("step_launches", ctypes.c_int64), ("variant", ctypes.c_int32), ("n_variants", ctypes.c_int32),
+                ("variant_name", ctypes.c_char * 32)]
 
 
 _SIGS = {
@@ -90,6 +92,9 @@ _SIGS = {
     "ah_get_tau": ([ctypes.c_void_p], ctypes.c_double),
     "ah_get_info": ([ctypes.c_void_p, ctypes.POINTER(ah_info)], ctypes.c_int),
     "ah_destroy": ([ctypes.c_void_p], None),
+    "ah_variant_count": ([ctypes.c_int32], ctypes.c_int32),
+    "ah_set_variant": ([ctypes.c_void_p, ctypes.c_int32], ctypes.c_int),
+    "ah_autotune": ([ctypes.c_void_p, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)], ctypes.c_int),
 }
 
 
@@ -201,7 +206,23 @@ def ah_get_tau(h) -> float:
 def ah_get_info(h) -> dict:
     i = ah_info()
     _check(load().ah_get_info(h, ctypes.byref(i)))
-    return {n: getattr(i, n) for n, _ in i._fields_}
+    d = {n: getattr(i, n) for n, _ in i._fields_}
+    d["variant_name"] = d["variant_name"].decode()
+    return d
+
+
+def ah_variant_count(precision: int) -> int:
+    return load().ah_variant_count(precision)
+
+
+def ah_set_variant(h, variant: int):
+    _check(load().ah_set_variant(h, variant))
+
+
+def ah_autotune(h, trial_steps: int = 3) -> int:
+    v = ctypes.c_int32(-1)
+    _check(load().ah_autotune(h, trial_steps, ctypes.byref(v)))
+    return v.value
 
 
 def ah_destroy(h):
@@ -248,6 +269,13 @@ class Sim:
 
     def set_fields(self, f: np.ndarray, step: int = 0):
         ah_set_fields(self.h, f, step)
+
+    def set_variant(self, variant: int):
+        ah_set_variant(self.h, variant)
+        return self
+
+    def autotune(self, trial_steps: int = 3) -> int:
+        return ah_autotune(self.h, trial_steps)
 
     def sync(self):
         ah_sync(self.h)

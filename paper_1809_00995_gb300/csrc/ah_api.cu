@@ -5,12 +5,16 @@
 // and of the diagnostics, and enqueues the kernels.  No arithmetic of the
 // method runs on the host besides those scalar coefficients and the final
 // combination of the FP64 sums into the observables.
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
 #include <new>
+#include <map>
+#include <mutex>
 #include <string>
+#include <tuple>
 
 #include "../../include/ah.h"
 #include "ah_internal.cuh"
@@ -111,7 +115,11 @@ struct ah_sim {
     DiagPartial *partials;
     DiagPartial *result;
     DiagPartial *host_result;
+    unsigned long long *host_count;
+    DiagList list;
     int diag_blocks;
+    int variant;
+    bool pristine;     // state is the freshly initialised random-phase state
     cudaStream_t stream;
     bool own_stream;
 };
@@ -158,7 +166,7 @@ ah_status validate(const ah_config &c)
         return fail(AH_ERR_ARG, "unknown precision %d", c.precision);
     if (c.kernel < AH_KERNEL_AUTO || c.kernel > AH_KERNEL_FUSED)
         return fail(AH_ERR_ARG, "unknown kernel %d", c.kernel);
-    if (c.flags != 0) return fail(AH_ERR_ARG, "flags must be 0");
+    if (c.flags & ~(AH_FLAG_EXACT_DIAG | AH_FLAG_AUTOTUNE)) return fail(AH_ERR_ARG, "unknown flags 0x%x", c.flags);
     if (!std::isfinite(c.s)) return fail(AH_ERR_ARG, "s must be finite");
     if (c.era != AH_MINKOWSKI && !(c.tau0 > 0)) return fail(AH_ERR_ARG, "tau0 must be > 0");
     if (!(c.tau_ref > 0)) return fail(AH_ERR_ARG, "tau_ref must be > 0");
@@ -185,7 +193,7 @@ ah_status do_step(ah_sim *h, int64_t n)
     if (h->cfg.kernel == AH_KERNEL_PLAIN) {
         AH_CUDA(launch_plain_step<real>(make_view(F, h->cur, false), h->N, k, h->stream));
     } else {
-        AH_CUDA(launch_fused_step<real>(make_view(F, h->cur, true), h->N, k, h->stream));
+        AH_CUDA(launch_fused_step<real>(make_view(F, h->cur, true), h->N, k, h->variant, h->stream));
         h->cur ^= 1;
     }
     return AH_OK;
@@ -196,11 +204,23 @@ ah_status do_diag(ah_sim *h, Box b, ah_obs *out)
 {
     Fields<real> &F = *(Fields<real> *)(h->cfg.precision == AH_FP32 ? (void *)&h->f32 : (void *)&h->f64);
     const DiagCoef dc = diag_coef(h->cfg, h->step);
-    AH_CUDA(launch_diag<real>(make_view(F, h->cur, false), h->N, b, dc, h->partials, h->diag_blocks,
-                              h->result, h->stream));
+    const View<real> v = make_view(F, h->cur, false);
+    const bool exact = (h->cfg.flags & AH_FLAG_EXACT_DIAG) != 0;
+    AH_CUDA(launch_diag<real>(v, h->N, b, dc, h->partials, h->diag_blocks, h->result, h->list, exact,
+                              h->stream));
     AH_CUDA(cudaMemcpyAsync(h->host_result, h->result, sizeof(DiagPartial), cudaMemcpyDeviceToHost,
                             h->stream));
+    AH_CUDA(cudaMemcpyAsync(h->host_count, h->list.count, sizeof(unsigned long long),
+                            cudaMemcpyDeviceToHost, h->stream));
     AH_CUDA(cudaStreamSynchronize(h->stream));
+    if (!exact && *h->host_count > (unsigned long long)h->list.capacity) {
+        // too many plaquettes near a branch cut for the list: redo all in FP64
+        AH_CUDA(launch_diag<real>(v, h->N, b, dc, h->partials, h->diag_blocks, h->result, h->list, true,
+                                  h->stream));
+        AH_CUDA(cudaMemcpyAsync(h->host_result, h->result, sizeof(DiagPartial), cudaMemcpyDeviceToHost,
+                                h->stream));
+        AH_CUDA(cudaStreamSynchronize(h->stream));
+    }
     const DiagPartial &r = *h->host_result;
     const ah_config &c = h->cfg;
     ah_obs o;
@@ -237,6 +257,40 @@ ah_status do_diag(ah_sim *h, Box b, ah_obs *out)
     return AH_OK;
 }
 
+// Random-phase initial state (Sec. 2): zero everything, then phi of buffer 0.
+cudaError_t write_initial_state(ah_sim *h)
+{
+    h->cur = 0;
+    h->step = 0;
+    h->pristine = true;
+    cudaError_t e = cudaMemsetAsync(h->dmem, 0, h->dbytes, h->stream);
+    if (e != cudaSuccess) return e;
+    if (h->cfg.precision == AH_FP32)
+        return launch_init_phase<float>(h->f32.phr[0], h->f32.phi[0], h->N, h->cfg.seed, h->cfg.sigma, h->stream);
+    return launch_init_phase<double>(h->f64.phr[0], h->f64.phi[0], h->N, h->cfg.seed, h->cfg.sigma, h->stream);
+}
+
+int n_variants(int precision)
+{
+    return precision == AH_FP32 ? fused_variant_count<float>() : fused_variant_count<double>();
+}
+
+// process-wide autotune results per (device, N, precision)
+std::mutex g_tune_mu;
+std::map<std::tuple<int, int, int>, int> g_tune;
+
+int tune_cache_get(const ah_sim *h)
+{
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tune.find(std::make_tuple(h->device, h->N, h->cfg.precision));
+    return it == g_tune.end() ? -1 : it->second;
+}
+void tune_cache_put(const ah_sim *h, int v)
+{
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune[std::make_tuple(h->device, h->N, h->cfg.precision)] = v;
+}
+
 ah_status enter(const ah_sim *h)
 {
     if (!h) return fail(AH_ERR_ARG, "null simulation handle");
@@ -248,7 +302,7 @@ ah_status enter(const ah_sim *h)
 
 extern "C" {
 
-int ah_abi_version(void) { return 1; }
+int ah_abi_version(void) { return 2; }
 
 const char *ah_last_error(void) { return g_err.c_str(); }
 
@@ -297,29 +351,38 @@ ah_status ah_create_ex(const ah_config *cfg, ah_sim **out)
     const size_t esz = cfg->precision == AH_FP32 ? sizeof(float) : sizeof(double);
     h->dbytes = 15 * padded((size_t)h->nsites) * esz;
     h->diag_blocks = diag_grid_blocks(h->num_sms);
+    // expected near-cut plaquettes: about 5e-5 of the 3 N^3 plaquettes in FP32
+    h->list.capacity = std::max<long long>(1LL << 20, h->nsites * 3 / 2000);
     e = cudaMalloc(&h->dmem, h->dbytes);
     if (e == cudaSuccess) e = cudaMalloc((void **)&h->partials, sizeof(DiagPartial) * (h->diag_blocks + 1));
-    if (e == cudaSuccess) e = cudaMallocHost((void **)&h->host_result, sizeof(DiagPartial));
+    if (e == cudaSuccess)
+        e = cudaMalloc((void **)&h->list.count, sizeof(unsigned long long) * (1 + h->list.capacity));
+    if (e == cudaSuccess) e = cudaMallocHost((void **)&h->host_result, sizeof(DiagPartial) + 16);
     if (e != cudaSuccess) {
         ah_destroy(h);
         return fail(AH_ERR_OOM, "allocation of %.3g GB failed: %s", h->dbytes / 1e9, cudaGetErrorString(e));
     }
     h->result = h->partials + h->diag_blocks;
-    e = cudaMemsetAsync(h->dmem, 0, h->dbytes, h->stream);
-    if (e == cudaSuccess) {
-        if (cfg->precision == AH_FP32) {
-            carve(h->f32, (char *)h->dmem, (size_t)h->nsites);
-            e = launch_init_phase<float>(h->f32.phr[0], h->f32.phi[0], h->N, cfg->seed, cfg->sigma, h->stream);
-        } else {
-            carve(h->f64, (char *)h->dmem, (size_t)h->nsites);
-            e = launch_init_phase<double>(h->f64.phr[0], h->f64.phi[0], h->N, cfg->seed, cfg->sigma, h->stream);
-        }
-    }
+    h->list.items = h->list.count + 1;
+    h->host_count = (unsigned long long *)(h->host_result + 1);
+    if (cfg->precision == AH_FP32) carve(h->f32, (char *)h->dmem, (size_t)h->nsites);
+    else carve(h->f64, (char *)h->dmem, (size_t)h->nsites);
+    e = write_initial_state(h);
     if (e != cudaSuccess) {
         ah_destroy(h);
         return fail(AH_ERR_CUDA, "initialisation failed: %s", cudaGetErrorString(e));
     }
     *out = h;
+    if (cfg->flags & AH_FLAG_AUTOTUNE) {
+        const int cached = tune_cache_get(h);
+        if (cached >= 0) {
+            h->variant = cached;
+        } else if ((st = ah_autotune(h, 3, nullptr)) != AH_OK) {
+            ah_destroy(h);
+            *out = nullptr;
+            return st;
+        }
+    }
     return AH_OK;
 }
 
@@ -346,6 +409,7 @@ ah_status ah_step(ah_sim *h, int64_t nsteps)
     ah_status st = enter(h);
     if (st != AH_OK) return st;
     if (nsteps < 0) return fail(AH_ERR_ARG, "nsteps must be >= 0");
+    if (nsteps > 0) h->pristine = false;
     for (int64_t q = 0; q < nsteps; ++q) {
         st = h->cfg.precision == AH_FP32 ? do_step<float>(h, h->step) : do_step<double>(h, h->step);
         if (st != AH_OK) return st;
@@ -414,6 +478,7 @@ ah_status ah_set_fields(ah_sim *h, const double *in, int64_t step)
     cudaFree(tmp);
     if (e != cudaSuccess) return fail(AH_ERR_CUDA, "set_fields failed: %s", cudaGetErrorString(e));
     h->step = step;
+    h->pristine = false;
     return AH_OK;
 }
 
@@ -456,6 +521,67 @@ ah_status ah_get_info(const ah_sim *h, ah_info *out)
     out->state_bytes = (int64_t)h->dbytes;
     out->step_bytes = 20 * esz * h->nsites;
     out->step_launches = h->cfg.kernel == AH_KERNEL_PLAIN ? 3 : 1;
+    out->variant = h->variant;
+    out->n_variants = n_variants(h->cfg.precision);
+    const char *nm = h->cfg.precision == AH_FP32 ? fused_variant_name<float>(h->variant)
+                                                 : fused_variant_name<double>(h->variant);
+    snprintf(out->variant_name, sizeof out->variant_name, "%s", h->cfg.kernel == AH_KERNEL_PLAIN ? "plain" : nm);
+    return AH_OK;
+}
+
+int32_t ah_variant_count(int32_t precision)
+{
+    return precision == AH_FP32 || precision == AH_FP64 ? n_variants(precision) : 0;
+}
+
+ah_status ah_set_variant(ah_sim *h, int32_t variant)
+{
+    if (!h) return fail(AH_ERR_ARG, "null simulation handle");
+    if (variant < 0 || variant >= n_variants(h->cfg.precision))
+        return fail(AH_ERR_ARG, "variant %d outside [0, %d)", variant, n_variants(h->cfg.precision));
+    h->variant = variant;
+    return AH_OK;
+}
+
+ah_status ah_autotune(ah_sim *h, int32_t trial_steps, int32_t *chosen)
+{
+    ah_status st = enter(h);
+    if (st != AH_OK) return st;
+    if (!h->pristine) return fail(AH_ERR_BUSY, "autotune needs the freshly created state");
+    if (trial_steps < 1) return fail(AH_ERR_ARG, "trial_steps must be >= 1");
+    if (h->cfg.kernel == AH_KERNEL_PLAIN) {
+        if (chosen) *chosen = h->variant;
+        return AH_OK;
+    }
+    cudaEvent_t e0, e1;
+    AH_CUDA(cudaEventCreate(&e0));
+    AH_CUDA(cudaEventCreate(&e1));
+    const int nv = n_variants(h->cfg.precision);
+    int best = 0;
+    float best_ms = 0.0f;
+    for (int v = 0; v < nv && st == AH_OK; ++v) {
+        h->variant = v;
+        // one untimed step (first launch configures the kernel), then trial_steps timed
+        st = h->cfg.precision == AH_FP32 ? do_step<float>(h, 0) : do_step<double>(h, 0);
+        if (st != AH_OK) break;
+        cudaEventRecord(e0, h->stream);
+        for (int q = 0; q < trial_steps && st == AH_OK; ++q)
+            st = h->cfg.precision == AH_FP32 ? do_step<float>(h, 0) : do_step<double>(h, 0);
+        cudaEventRecord(e1, h->stream);
+        cudaError_t ce = cudaEventSynchronize(e1);
+        if (ce != cudaSuccess) { st = fail(AH_ERR_CUDA, "autotune: %s", cudaGetErrorString(ce)); break; }
+        float ms = 0.0f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (v == 0 || ms < best_ms) { best = v; best_ms = ms; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st != AH_OK) return st;
+    h->variant = best;
+    tune_cache_put(h, best);
+    AH_CUDA(write_initial_state(h));
+    AH_CUDA(cudaStreamSynchronize(h->stream));
+    if (chosen) *chosen = best;
     return AH_OK;
 }
 
@@ -466,6 +592,7 @@ void ah_destroy(ah_sim *h)
     if (h->stream) cudaStreamSynchronize(h->stream);
     if (h->dmem) cudaFree(h->dmem);
     if (h->partials) cudaFree(h->partials);
+    if (h->list.count) cudaFree(h->list.count);
     if (h->host_result) cudaFreeHost(h->host_result);
     if (h->stream && h->own_stream) cudaStreamDestroy(h->stream);
     delete h;

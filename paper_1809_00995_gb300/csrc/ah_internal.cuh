@@ -61,6 +61,14 @@ struct DiagPartial {
 
 struct Box { int x0, y0, z0, nx, ny, nz; };
 
+// Plaquettes whose winding the fast diagnostics leave to the FP64 path:
+// items[k] = site index * 4 + orientation (0: 12, 1: 13, 2: 23).
+struct DiagList {
+    unsigned long long *count;
+    unsigned long long *items;
+    long long capacity;
+};
+
 // ---- launchers (each returns the launch's cudaError_t) ----
 template <typename real>
 cudaError_t launch_init_phase(real *phr, real *phi, int N, uint64_t seed, double sigma,
@@ -78,14 +86,19 @@ template <typename real>
 cudaError_t launch_plain_step(const View<real> &v, int N, const KickCoef<real> &c,
                               cudaStream_t st);
 
+// Fused step, compile-time shape `variant` in [0, fused_variant_count<real>()).
 template <typename real>
-cudaError_t launch_fused_step(const View<real> &v, int N, const KickCoef<real> &c,
+cudaError_t launch_fused_step(const View<real> &v, int N, const KickCoef<real> &c, int variant,
                               cudaStream_t st);
+template <typename real>
+int fused_variant_count();
+template <typename real>
+const char *fused_variant_name(int variant);
 
 template <typename real>
 cudaError_t launch_diag(const View<real> &v, int N, Box b, const DiagCoef &c,
                         DiagPartial *partials, int nblocks, DiagPartial *result,
-                        cudaStream_t st);
+                        DiagList list, bool exact, cudaStream_t st);
 
 int diag_grid_blocks(int num_sms);
 

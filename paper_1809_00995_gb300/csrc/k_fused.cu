@@ -19,15 +19,13 @@
 // state exactly once from DRAM; halo re-reads are served by L2.  Periodic
 // boundaries are applied in the index arithmetic.
 #include "ah_internal.cuh"
+#include "sincos32.cuh"
 
 namespace ah {
 namespace {
 
 template <typename real>
 struct cpx { real r, i; };
-
-__device__ __forceinline__ void sc(float t, float *s, float *c) { sincosf(t, s, c); }
-__device__ __forceinline__ void sc(double t, double *s, double *c) { sincos(t, s, c); }
 
 template <typename real>
 __device__ __forceinline__ cpx<real> mul(cpx<real> a, cpx<real> b)
@@ -59,8 +57,8 @@ struct Geo {
     static_assert(TY % 8 == 0 && NHALO <= NT && NPHALO <= NT, "tile shape");
 };
 
-template <typename real, int TY>
-__global__ void __launch_bounds__(256) k_fused(View<real> v, int N, int zc, KickCoef<real> c)
+template <typename real, int TY, int MINB>
+__global__ void __launch_bounds__(256, MINB) k_fused(View<real> v, int N, int zc, KickCoef<real> c)
 {
     using G = Geo<real, TY>;
     constexpr int TX = G::TX, RY = G::RY, EX = G::EX, EY = G::EY, NE = G::NE, PX = G::PX;
@@ -120,7 +118,7 @@ __global__ void __launch_bounds__(256) k_fused(View<real> v, int N, int zc, Kick
 #pragma unroll
                 for (int d = 0; d < 3; ++d) {
                     real s, co;
-                    sc(fth[t][d], &s, &co);
+                    sincos_link(fth[t][d], &s, &co);
                     sU[(b * 3 + d) * NE + eix[t]] = { co, s };
                 }
                 sF[b * NE + eix[t]] = { fph[t][0], fph[t][1] };
@@ -256,38 +254,73 @@ __global__ void __launch_bounds__(256) k_fused(View<real> v, int N, int zc, Kick
     }
 }
 
-template <typename real, int TY>
-cudaError_t launch_ty(const View<real> &v, int N, const KickCoef<real> &c, cudaStream_t st)
+// Compile-time shapes of the fused step: tile height TY (32 x TY sites, 256
+// threads, TY/8 sites per thread) and the minimum number of resident CTAs per SM
+// the register allocation must allow.
+struct VariantInfo { int ty, minb, min_chunk; const char *name; };
+constexpr VariantInfo kVariants32[] = {
+    { 16, 2, 16, "ty16_b2" }, { 16, 3, 16, "ty16_b3" }, { 8, 4, 16, "ty8_b4" },
+    { 8, 3, 16, "ty8_b3" },  { 32, 1, 16, "ty32_b1" }, { 16, 2, 64, "ty16_b2_z64" },
+};
+constexpr VariantInfo kVariants64[] = { { 16, 1, 16, "ty16_b1" }, { 8, 2, 16, "ty8_b2" } };
+
+template <typename real, int TY, int MINB>
+cudaError_t launch_shape(const View<real> &v, int N, const KickCoef<real> &c, int min_chunk, cudaStream_t st)
 {
     using G = Geo<real, TY>;
-    static bool configured = false;   // per (real, TY) instantiation
+    static bool configured = false;   // once per instantiation
     if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(k_fused<real, TY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaError_t e = cudaFuncSetAttribute(k_fused<real, TY, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)G::smem);
         if (e != cudaSuccess) return e;
         configured = true;
     }
     const int tx = (N + G::TX - 1) / G::TX, ty = (N + TY - 1) / TY;
-    // enough z chunks for several waves of CTAs, chunks of at least 16 planes
+    // enough z chunks for several waves of CTAs, chunks of at least min_chunk planes
     int nch = (int)((152LL * 16 + (long long)tx * ty - 1) / ((long long)tx * ty));
-    nch = max(1, min(nch, N / 16));
+    nch = max(1, min(nch, N / min_chunk));
     const int zc = (N + nch - 1) / nch;
     nch = (N + zc - 1) / zc;
-    k_fused<real, TY><<<dim3(tx, ty, nch), G::NT, G::smem, st>>>(v, N, zc, c);
+    k_fused<real, TY, MINB><<<dim3(tx, ty, nch), G::NT, G::smem, st>>>(v, N, zc, c);
     return cudaGetLastError();
 }
 
 }  // namespace
 
 template <>
-cudaError_t launch_fused_step<float>(const View<float> &v, int N, const KickCoef<float> &c, cudaStream_t st)
+int fused_variant_count<float>() { return (int)(sizeof(kVariants32) / sizeof(kVariants32[0])); }
+template <>
+int fused_variant_count<double>() { return (int)(sizeof(kVariants64) / sizeof(kVariants64[0])); }
+template <>
+const char *fused_variant_name<float>(int k) { return kVariants32[k].name; }
+template <>
+const char *fused_variant_name<double>(int k) { return kVariants64[k].name; }
+
+template <>
+cudaError_t launch_fused_step<float>(const View<float> &v, int N, const KickCoef<float> &c, int variant,
+                                     cudaStream_t st)
 {
-    return launch_ty<float, 16>(v, N, c, st);
+    const int mc = kVariants32[variant].min_chunk;
+    switch (variant) {
+    case 0: return launch_shape<float, 16, 2>(v, N, c, mc, st);
+    case 1: return launch_shape<float, 16, 3>(v, N, c, mc, st);
+    case 2: return launch_shape<float, 8, 4>(v, N, c, mc, st);
+    case 3: return launch_shape<float, 8, 3>(v, N, c, mc, st);
+    case 4: return launch_shape<float, 32, 1>(v, N, c, mc, st);
+    case 5: return launch_shape<float, 16, 2>(v, N, c, mc, st);
+    default: return cudaErrorInvalidValue;
+    }
 }
 template <>
-cudaError_t launch_fused_step<double>(const View<double> &v, int N, const KickCoef<double> &c, cudaStream_t st)
+cudaError_t launch_fused_step<double>(const View<double> &v, int N, const KickCoef<double> &c, int variant,
+                                      cudaStream_t st)
 {
-    return launch_ty<double, 16>(v, N, c, st);
+    const int mc = kVariants64[variant].min_chunk;
+    switch (variant) {
+    case 0: return launch_shape<double, 16, 1>(v, N, c, mc, st);
+    case 1: return launch_shape<double, 8, 2>(v, N, c, mc, st);
+    default: return cudaErrorInvalidValue;
+    }
 }
 
 }  // namespace ah

@@ -1,0 +1,47 @@
+// sincos32.cuh -- single-precision sine and cosine of a link phase.
+//
+// Method (Cody & Waite's additive range reduction, written with fused
+// multiply-adds): k = nearest integer to t * 2/pi, r = t - k pi/2 with pi/2
+// split into three FP32 parts P1 + P2 + P3 (P1 = fl(pi/2), P2 = fl(pi/2 - P1),
+// P3 = fl(pi/2 - P1 - P2); |pi/2 - P1 - P2 - P3| < 1.1e-23), so r is exact to
+// an ulp for the arguments of this code.  On |r| <= pi/4 the Taylor
+// polynomials of sin (through r^9) and cos (through r^10) leave truncation
+// errors below |r|^11/11! < 2e-9 and |r|^12/12! < 2e-10; the quadrant k mod 4
+// then selects and signs the two.  Arguments with |t| >= 2^17 (never reached by
+// a link phase of this code in practice) go to the library sincosf.
+#pragma once
+
+namespace ah {
+
+__device__ __forceinline__ void sincos_link(float t, float *s, float *c)
+{
+    if (!(fabsf(t) < 131072.0f)) {
+        sincosf(t, s, c);
+        return;
+    }
+    const float kf = rintf(t * 0x1.45f306p-1f);          // 2/pi
+    float r = fmaf(-kf, 0x1.921fb6p+0f, t);               // P1
+    r = fmaf(-kf, -0x1.777a5cp-25f, r);                   // P2
+    r = fmaf(-kf, -0x1.ee59dap-50f, r);                   // P3
+    const float r2 = r * r;
+    // sin r = r + r^3 (-1/3! + r^2 (1/5! + r^2 (-1/7! + r^2 / 9!)))
+    float ps = fmaf(r2, 2.755731884e-06f, -1.984127011e-04f);
+    ps = fmaf(r2, ps, 8.333333768e-03f);
+    ps = fmaf(r2, ps, -1.666666716e-01f);
+    const float sr = fmaf(r * r2, ps, r);
+    // cos r = 1 + r^2 (-1/2! + r^2 (1/4! + r^2 (-1/6! + r^2 (1/8! - r^2 / 10!))))
+    float pc = fmaf(r2, -2.755731998e-07f, 2.480158764e-05f);
+    pc = fmaf(r2, pc, -1.388888923e-03f);
+    pc = fmaf(r2, pc, 4.166666791e-02f);
+    pc = fmaf(r2, pc, -0.5f);
+    const float cr = fmaf(r2, pc, 1.0f);
+    const int q = (int)kf;
+    const float a = (q & 1) ? cr : sr;        // |sin t|
+    const float b = (q & 1) ? sr : cr;        // |cos t|
+    *s = (q & 2) ? -a : a;
+    *c = ((q + 1) & 2) ? -b : b;
+}
+
+__device__ __forceinline__ void sincos_link(double t, double *s, double *c) { sincos(t, s, c); }
+
+}  // namespace ah

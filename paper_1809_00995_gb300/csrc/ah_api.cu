@@ -15,6 +15,7 @@
 #include <mutex>
 #include <string>
 #include <tuple>
+#include <type_traits>
 
 #include "../../include/ah.h"
 #include "ah_internal.cuh"
@@ -120,6 +121,10 @@ struct ah_sim {
     int diag_blocks;
     int variant;
     bool pristine;     // state is the freshly initialised random-phase state
+    bool tma_ready;    // tensor maps built (FP32, N % 32 == 0)
+    TmaMaps tmaps[2];  // per read buffer (phi/theta ping-pong index)
+    int *d_err;        // device error word of the bounded waits
+    int *host_err;
     cudaStream_t stream;
     bool own_stream;
 };
@@ -185,6 +190,49 @@ ah_status validate(const ah_config &c)
     return AH_OK;
 }
 
+// FP32 shapes beyond the k_fused ones: the paired-arithmetic kernel (k_pair.cu)
+// and the TMA-fed kernel (resident CTAs per SM, minimum z-chunk length).
+struct TmaShape { int minb, min_chunk; const char *name; };
+constexpr TmaShape kTmaShapes[] = { { 3, 16, "tma_b3" }, { 2, 16, "tma_b2" }, { 3, 64, "tma_b3_z64" } };
+constexpr int kNumTma = (int)(sizeof(kTmaShapes) / sizeof(kTmaShapes[0]));
+constexpr const char *kPairNames[kPairShapes] = { "pair_ty6_b3", "pair_ty6_b4", "pair_ty14_b1", "pair_ty14_b2",
+                                                  "pair_ty30_b1" };
+
+int n_variants(int precision)
+{
+    return precision == AH_FP32 ? fused_variant_count<float>() + kPairShapes + kNumTma : fused_variant_count<double>();
+}
+// FP32 variant families: 0 k_fused, 1 k_pair, 2 k_fused_tma; *idx = index within the family
+int family(const ah_sim *h, int v, int *idx)
+{
+    if (h->cfg.precision != AH_FP32 || v < fused_variant_count<float>()) { *idx = v; return 0; }
+    v -= fused_variant_count<float>();
+    if (v < kPairShapes) { *idx = v; return 1; }
+    *idx = v - kPairShapes;
+    return 2;
+}
+bool variant_ok(const ah_sim *h, int v)
+{
+    if (v < 0 || v >= n_variants(h->cfg.precision)) return false;
+    int i;
+    switch (family(h, v, &i)) {
+    case 1: return pair_shape_ok(h->N);
+    case 2: return h->tma_ready;
+    default:
+        return h->cfg.precision == AH_FP32 ? fused_variant_ok<float>(v, h->N) : fused_variant_ok<double>(v, h->N);
+    }
+}
+const char *variant_name(const ah_sim *h, int v)
+{
+    if (h->cfg.precision == AH_FP64) return fused_variant_name<double>(v);
+    int i;
+    switch (family(h, v, &i)) {
+    case 1: return kPairNames[i];
+    case 2: return kTmaShapes[i].name;
+    default: return fused_variant_name<float>(v);
+    }
+}
+
 template <typename real>
 ah_status do_step(ah_sim *h, int64_t n)
 {
@@ -192,9 +240,34 @@ ah_status do_step(ah_sim *h, int64_t n)
     const KickCoef<real> k = kick_coef<real>(h->cfg, n);
     if (h->cfg.kernel == AH_KERNEL_PLAIN) {
         AH_CUDA(launch_plain_step<real>(make_view(F, h->cur, false), h->N, k, h->stream));
+    } else if (int idx; family(h, h->variant, &idx) != 0) {
+        if constexpr (std::is_same<real, float>::value) {
+            if (family(h, h->variant, &idx) == 1) {
+                AH_CUDA(launch_pair_step(make_view(F, h->cur, true), h->N, k, idx, h->stream));
+            } else {
+                const TmaShape &t = kTmaShapes[idx];
+                AH_CUDA(launch_fused_tma(h->tmaps[h->cur], make_view(F, h->cur, true), h->N, k, h->d_err, t.minb,
+                                         t.min_chunk, h->stream));
+            }
+            h->cur ^= 1;
+        }
     } else {
         AH_CUDA(launch_fused_step<real>(make_view(F, h->cur, true), h->N, k, h->variant, h->stream));
         h->cur ^= 1;
+    }
+    return AH_OK;
+}
+
+// Read and clear the device error word of the bounded waits (synchronous).
+ah_status check_device_error(ah_sim *h)
+{
+    if (!h->d_err) return AH_OK;
+    AH_CUDA(cudaMemcpyAsync(h->host_err, h->d_err, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    AH_CUDA(cudaStreamSynchronize(h->stream));
+    if (*h->host_err) {
+        *h->host_err = 0;
+        cudaMemsetAsync(h->d_err, 0, sizeof(int), h->stream);
+        return fail(AH_ERR_TIMEOUT, "a bounded wait in the fused step gave up; the state is not valid");
     }
     return AH_OK;
 }
@@ -212,7 +285,9 @@ ah_status do_diag(ah_sim *h, Box b, ah_obs *out)
                             h->stream));
     AH_CUDA(cudaMemcpyAsync(h->host_count, h->list.count, sizeof(unsigned long long),
                             cudaMemcpyDeviceToHost, h->stream));
+    AH_CUDA(cudaMemcpyAsync(h->host_err, h->d_err, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
     AH_CUDA(cudaStreamSynchronize(h->stream));
+    if (*h->host_err) return check_device_error(h);
     if (!exact && *h->host_count > (unsigned long long)h->list.capacity) {
         // too many plaquettes near a branch cut for the list: redo all in FP64
         AH_CUDA(launch_diag<real>(v, h->N, b, dc, h->partials, h->diag_blocks, h->result, h->list, true,
@@ -268,11 +343,6 @@ cudaError_t write_initial_state(ah_sim *h)
     if (h->cfg.precision == AH_FP32)
         return launch_init_phase<float>(h->f32.phr[0], h->f32.phi[0], h->N, h->cfg.seed, h->cfg.sigma, h->stream);
     return launch_init_phase<double>(h->f64.phr[0], h->f64.phi[0], h->N, h->cfg.seed, h->cfg.sigma, h->stream);
-}
-
-int n_variants(int precision)
-{
-    return precision == AH_FP32 ? fused_variant_count<float>() : fused_variant_count<double>();
 }
 
 // process-wide autotune results per (device, N, precision)
@@ -357,7 +427,7 @@ ah_status ah_create_ex(const ah_config *cfg, ah_sim **out)
     if (e == cudaSuccess) e = cudaMalloc((void **)&h->partials, sizeof(DiagPartial) * (h->diag_blocks + 1));
     if (e == cudaSuccess)
         e = cudaMalloc((void **)&h->list.count, sizeof(unsigned long long) * (1 + h->list.capacity));
-    if (e == cudaSuccess) e = cudaMallocHost((void **)&h->host_result, sizeof(DiagPartial) + 16);
+    if (e == cudaSuccess) e = cudaMallocHost((void **)&h->host_result, sizeof(DiagPartial) + 32);
     if (e != cudaSuccess) {
         ah_destroy(h);
         return fail(AH_ERR_OOM, "allocation of %.3g GB failed: %s", h->dbytes / 1e9, cudaGetErrorString(e));
@@ -365,8 +435,25 @@ ah_status ah_create_ex(const ah_config *cfg, ah_sim **out)
     h->result = h->partials + h->diag_blocks;
     h->list.items = h->list.count + 1;
     h->host_count = (unsigned long long *)(h->host_result + 1);
+    h->host_err = (int *)(h->host_count + 1);
+    e = cudaMalloc((void **)&h->d_err, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->d_err, 0, sizeof(int), h->stream);
+    if (e != cudaSuccess) {
+        ah_destroy(h);
+        return fail(AH_ERR_OOM, "allocation failed: %s", cudaGetErrorString(e));
+    }
     if (cfg->precision == AH_FP32) carve(h->f32, (char *)h->dmem, (size_t)h->nsites);
     else carve(h->f64, (char *)h->dmem, (size_t)h->nsites);
+    if (cfg->precision == AH_FP32 && tma_shape_ok(h->N)) {
+        cudaError_t me = cudaSuccess;
+        for (int b = 0; b < 2 && me == cudaSuccess; ++b) {
+            const float *fs[5] = { h->f32.phr[b], h->f32.phi[b], h->f32.th[b][0], h->f32.th[b][1], h->f32.th[b][2] };
+            const float *qs[5] = { h->f32.pir, h->f32.pii, h->f32.el[0], h->f32.el[1], h->f32.el[2] };
+            for (int k = 0; k < 5 && me == cudaSuccess; ++k) me = make_tma_map(&h->tmaps[b].f[k], fs[k], h->N);
+            for (int k = 0; k < 5 && me == cudaSuccess; ++k) me = make_tma_map(&h->tmaps[b].q[k], qs[k], h->N);
+        }
+        h->tma_ready = me == cudaSuccess;
+    }
     e = write_initial_state(h);
     if (e != cudaSuccess) {
         ah_destroy(h);
@@ -503,7 +590,7 @@ ah_status ah_sync(ah_sim *h)
     ah_status st = enter(h);
     if (st != AH_OK) return st;
     AH_CUDA(cudaStreamSynchronize(h->stream));
-    return AH_OK;
+    return check_device_error(h);
 }
 
 int64_t ah_get_step(const ah_sim *h) { return h ? h->step : -1; }
@@ -523,8 +610,7 @@ ah_status ah_get_info(const ah_sim *h, ah_info *out)
     out->step_launches = h->cfg.kernel == AH_KERNEL_PLAIN ? 3 : 1;
     out->variant = h->variant;
     out->n_variants = n_variants(h->cfg.precision);
-    const char *nm = h->cfg.precision == AH_FP32 ? fused_variant_name<float>(h->variant)
-                                                 : fused_variant_name<double>(h->variant);
+    const char *nm = variant_name(h, h->variant);
     snprintf(out->variant_name, sizeof out->variant_name, "%s", h->cfg.kernel == AH_KERNEL_PLAIN ? "plain" : nm);
     return AH_OK;
 }
@@ -537,8 +623,9 @@ int32_t ah_variant_count(int32_t precision)
 ah_status ah_set_variant(ah_sim *h, int32_t variant)
 {
     if (!h) return fail(AH_ERR_ARG, "null simulation handle");
-    if (variant < 0 || variant >= n_variants(h->cfg.precision))
-        return fail(AH_ERR_ARG, "variant %d outside [0, %d)", variant, n_variants(h->cfg.precision));
+    if (!variant_ok(h, variant))
+        return fail(AH_ERR_ARG, "variant %d not available (count %d, N=%d)", variant, n_variants(h->cfg.precision),
+                    h->N);
     h->variant = variant;
     return AH_OK;
 }
@@ -560,6 +647,7 @@ ah_status ah_autotune(ah_sim *h, int32_t trial_steps, int32_t *chosen)
     int best = 0;
     float best_ms = 0.0f;
     for (int v = 0; v < nv && st == AH_OK; ++v) {
+        if (!variant_ok(h, v)) continue;
         h->variant = v;
         // one untimed step (first launch configures the kernel), then trial_steps timed
         st = h->cfg.precision == AH_FP32 ? do_step<float>(h, 0) : do_step<double>(h, 0);
@@ -573,6 +661,7 @@ ah_status ah_autotune(ah_sim *h, int32_t trial_steps, int32_t *chosen)
         float ms = 0.0f;
         cudaEventElapsedTime(&ms, e0, e1);
         if (v == 0 || ms < best_ms) { best = v; best_ms = ms; }
+        if ((st = check_device_error(h)) != AH_OK) break;
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
@@ -593,6 +682,7 @@ void ah_destroy(ah_sim *h)
     if (h->dmem) cudaFree(h->dmem);
     if (h->partials) cudaFree(h->partials);
     if (h->list.count) cudaFree(h->list.count);
+    if (h->d_err) cudaFree(h->d_err);
     if (h->host_result) cudaFreeHost(h->host_result);
     if (h->stream && h->own_stream) cudaStreamDestroy(h->stream);
     delete h;

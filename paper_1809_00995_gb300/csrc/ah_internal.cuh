@@ -3,6 +3,7 @@
 #pragma once
 
 #include <cstdint>
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 namespace ah {
@@ -94,6 +95,8 @@ template <typename real>
 int fused_variant_count();
 template <typename real>
 const char *fused_variant_name(int variant);
+template <typename real>
+bool fused_variant_ok(int variant, int N);
 
 template <typename real>
 cudaError_t launch_diag(const View<real> &v, int N, Box b, const DiagCoef &c,
@@ -101,5 +104,24 @@ cudaError_t launch_diag(const View<real> &v, int N, Box b, const DiagCoef &c,
                         DiagList list, bool exact, cudaStream_t st);
 
 int diag_grid_blocks(int num_sms);
+
+// Fused step with paired FP32 arithmetic (N even), shapes 0..4.
+bool pair_shape_ok(int N);
+cudaError_t launch_pair_step(const View<float> &v, int N, const KickCoef<float> &c, int shape, cudaStream_t st);
+constexpr int kPairShapes = 5;
+
+// TMA-fed fused step (FP32, N % 32 == 0): tensor maps of the interior boxes of
+// the read buffer (phi.re, phi.im, theta_1..3) and of Pi.re, Pi.im, E_1..3.
+struct TmaMaps {
+    CUtensorMap f[5];
+    CUtensorMap q[5];
+};
+bool tma_shape_ok(int N);
+size_t tma_smem_bytes();
+cudaError_t make_tma_map(CUtensorMap *m, const float *base, int N);
+// minb: resident CTAs per SM the registers must allow (2 or 3); *err is set to 1
+// if a bounded wait gave up.
+cudaError_t launch_fused_tma(const TmaMaps &maps, const View<float> &v, int N, const KickCoef<float> &c,
+                             int *err, int minb, int min_chunk, cudaStream_t st);
 
 }  // namespace ah

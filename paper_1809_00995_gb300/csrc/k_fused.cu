@@ -46,9 +46,9 @@ __device__ __forceinline__ int wrapm(int a, int N)
     return a < 0 ? a + N : a;
 }
 
-template <typename real, int TY>
+template <typename real, int TY, int RX>
 struct Geo {
-    static constexpr int TX = 32, NT = 256, RY = TY / 8;
+    static constexpr int TX = 32 * RX, NT = 256, RY = TY / 8, NS = RX * RY;
     static constexpr int EX = TX + 2, EY = TY + 2, NE = EX * EY;
     static constexpr int NHALO = 2 * EX + 2 * TY;
     static constexpr int PX = TX + 1, PY = TY + 1, NP = PX * PY;
@@ -57,11 +57,33 @@ struct Geo {
     static_assert(TY % 8 == 0 && NHALO <= NT && NPHALO <= NT, "tile shape");
 };
 
-template <typename real, int TY, int MINB>
+// RX consecutive reals of one row (vector access when RX = 2; the pair never
+// straddles the end of a row because N is even for these shapes).
+template <typename real, int RX> struct Row;
+template <typename real> struct Row<real, 1> {
+    static __device__ __forceinline__ void ld(const real *p, real *o) { o[0] = *p; }
+    static __device__ __forceinline__ void st(real *p, const real *i) { *p = i[0]; }
+};
+template <> struct Row<float, 2> {
+    static __device__ __forceinline__ void ld(const float *p, float *o)
+    { const float2 t = *reinterpret_cast<const float2 *>(p); o[0] = t.x; o[1] = t.y; }
+    static __device__ __forceinline__ void st(float *p, const float *i)
+    { *reinterpret_cast<float2 *>(p) = make_float2(i[0], i[1]); }
+};
+template <> struct Row<double, 2> {
+    static __device__ __forceinline__ void ld(const double *p, double *o)
+    { const double2 t = *reinterpret_cast<const double2 *>(p); o[0] = t.x; o[1] = t.y; }
+    static __device__ __forceinline__ void st(double *p, const double *i)
+    { *reinterpret_cast<double2 *>(p) = make_double2(i[0], i[1]); }
+};
+
+// Each thread owns RX consecutive sites in x times RY rows (y stride 8).
+template <typename real, int TY, int RX, int MINB>
 __global__ void __launch_bounds__(256, MINB) k_fused(View<real> v, int N, int zc, KickCoef<real> c)
 {
-    using G = Geo<real, TY>;
-    constexpr int TX = G::TX, RY = G::RY, EX = G::EX, EY = G::EY, NE = G::NE, PX = G::PX;
+    using G = Geo<real, TY, RX>;
+    using IO = Row<real, RX>;
+    constexpr int TX = G::TX, RY = G::RY, NS = G::NS, EX = G::EX, EY = G::EY, NE = G::NE, PX = G::PX;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     cpx<real> *sU = reinterpret_cast<cpx<real> *>(smem_raw);   // [2 planes][3 dirs][NE]
     cpx<real> *sF = sU + 2 * 3 * NE;                            // [2 planes][NE] phi
@@ -74,18 +96,20 @@ __global__ void __launch_bounds__(256, MINB) k_fused(View<real> v, int N, int zc
     const int z1 = min(z0 + zc, N);
     const long long NN = (long long)N * N;
 
-    // In-plane offsets and extended-tile slots of this thread's tasks: its RY own
-    // sites, then (for tid < NHALO) one site of the halo ring.
-    int off[RY + 1], eix[RY + 1];
+    // own rows: in-plane offset of the first of the RX sites, validity
+    int roff[RY];
     bool wr[RY];
 #pragma unroll
-    for (int m = 0; m < RY; ++m) {
-        const int gx = x0 + lx, gy = y0 + wy + 8 * m;
-        wr[m] = gx < N && gy < N;
-        off[m] = wrapm(gx, N) + N * wrapm(gy, N);
-        eix[m] = (wy + 8 * m + 1) * EX + lx + 1;
+    for (int my = 0; my < RY; ++my) {
+        const int gx = x0 + RX * lx, gy = y0 + wy + 8 * my;
+        wr[my] = gx < N && gy < N;
+        roff[my] = wrapm(gx, N) + N * wrapm(gy, N);
     }
+    auto eix = [&](int m) { return (wy + 8 * (m / RX) + 1) * EX + RX * lx + (m % RX) + 1; };
+    auto pix = [&](int m) { return (wy + 8 * (m / RX) + 1) * PX + RX * lx + (m % RX) + 1; };
+    // halo task (tid < NHALO): one site of the halo ring
     const bool has_halo = tid < G::NHALO;
+    int hoff, heix;
     {
         int ex = 0, ey = 0;
         const int h = tid;
@@ -93,61 +117,79 @@ __global__ void __launch_bounds__(256, MINB) k_fused(View<real> v, int N, int zc
         else if (h < 2 * EX) { ex = h - EX; ey = EY - 1; }
         else if (h < 2 * EX + TY) { ex = 0; ey = 1 + h - 2 * EX; }
         else { ex = EX - 1; ey = 1 + h - 2 * EX - TY; }
-        off[RY] = wrapm(x0 + ex - 1, N) + N * wrapm(y0 + ey - 1, N);
-        eix[RY] = ey * EX + ex;
+        hoff = wrapm(x0 + ex - 1, N) + N * wrapm(y0 + ey - 1, N);
+        heix = ey * EX + ex;
     }
 
-    // register prefetch of one plane's phi, theta for every task
-    real fth[RY + 1][3], fph[RY + 1][2];
+    // register prefetch of one plane's phi, theta: own sites [0, NS), halo [NS]
+    real fth[NS + 1][3], fph[NS + 1][2];
     auto load_plane = [&](int z) {
         const long long base = (long long)wrapm(z, N) * NN;
 #pragma unroll
-        for (int t = 0; t <= RY; ++t) {
-            if (t < RY || has_halo) {
-                const long long s = base + off[t];
-                fth[t][0] = v.th1[s]; fth[t][1] = v.th2[s]; fth[t][2] = v.th3[s];
-                fph[t][0] = v.phr[s]; fph[t][1] = v.phi[s];
-            }
+        for (int my = 0; my < RY; ++my) {
+            const long long s = base + roff[my];
+            real t[RX];
+            IO::ld(v.th1 + s, t);
+#pragma unroll
+            for (int mx = 0; mx < RX; ++mx) fth[my * RX + mx][0] = t[mx];
+            IO::ld(v.th2 + s, t);
+#pragma unroll
+            for (int mx = 0; mx < RX; ++mx) fth[my * RX + mx][1] = t[mx];
+            IO::ld(v.th3 + s, t);
+#pragma unroll
+            for (int mx = 0; mx < RX; ++mx) fth[my * RX + mx][2] = t[mx];
+            IO::ld(v.phr + s, t);
+#pragma unroll
+            for (int mx = 0; mx < RX; ++mx) fph[my * RX + mx][0] = t[mx];
+            IO::ld(v.phi + s, t);
+#pragma unroll
+            for (int mx = 0; mx < RX; ++mx) fph[my * RX + mx][1] = t[mx];
+        }
+        if (has_halo) {
+            const long long s = base + hoff;
+            fth[NS][0] = v.th1[s]; fth[NS][1] = v.th2[s]; fth[NS][2] = v.th3[s];
+            fph[NS][0] = v.phr[s]; fph[NS][1] = v.phi[s];
         }
     };
     // U and phi of the prefetched plane into shared buffer b
     auto store_plane = [&](int b) {
 #pragma unroll
-        for (int t = 0; t <= RY; ++t) {
-            if (t < RY || has_halo) {
+        for (int t = 0; t <= NS; ++t) {
+            if (t < NS || has_halo) {
+                const int e = t < NS ? eix(t) : heix;
 #pragma unroll
                 for (int d = 0; d < 3; ++d) {
-                    real s, co;
-                    sincos_link(fth[t][d], &s, &co);
-                    sU[(b * 3 + d) * NE + eix[t]] = { co, s };
+                    real sn, co;
+                    sincos_link(fth[t][d], &sn, &co);
+                    sU[(b * 3 + d) * NE + e] = { co, sn };
                 }
-                sF[b * NE + eix[t]] = { fph[t][0], fph[t][1] };
+                sF[b * NE + e] = { fph[t][0], fph[t][1] };
             }
         }
     };
 
     // own-site registers carried along z
-    cpx<real> ph_m[RY], ph_0[RY], u3_m[RY];
-    real th_0[RY][3], p13_m[RY], p23_m[RY];
+    cpx<real> ph_m[NS], ph_0[NS], u3_m[NS];
+    real th_0[NS][3], p13_m[NS], p23_m[NS];
 
     // prologue: planes z0-1 and z0
     load_plane(z0 - 1);
     const int bm = (z0 - 1) & 1, b0 = z0 & 1;
     store_plane(bm);
 #pragma unroll
-    for (int m = 0; m < RY; ++m) ph_m[m] = { fph[m][0], fph[m][1] };
+    for (int m = 0; m < NS; ++m) ph_m[m] = { fph[m][0], fph[m][1] };
     load_plane(z0);
     store_plane(b0);
 #pragma unroll
-    for (int m = 0; m < RY; ++m) {
+    for (int m = 0; m < NS; ++m) {
         ph_0[m] = { fph[m][0], fph[m][1] };
         th_0[m][0] = fth[m][0]; th_0[m][1] = fth[m][1]; th_0[m][2] = fth[m][2];
     }
     load_plane(z0 + 1);
     __syncthreads();
 #pragma unroll
-    for (int m = 0; m < RY; ++m) {
-        const int e = eix[m];
+    for (int m = 0; m < NS; ++m) {
+        const int e = eix(m);
         const cpx<real> *Um = sU + bm * 3 * NE, *U0 = sU + b0 * 3 * NE;
         u3_m[m] = Um[2 * NE + e];
         p13_m[m] = plaq(Um[e], Um[2 * NE + e + 1], U0[e], Um[2 * NE + e]);
@@ -159,19 +201,22 @@ __global__ void __launch_bounds__(256, MINB) k_fused(View<real> v, int N, int zc
         const int bc = z & 1, bn = (z + 1) & 1;
         const long long base = (long long)z * NN;
         // Pi, E of plane z (consumed after two barriers)
-        real pr[RY], pim[RY], e1[RY], e2[RY], e3[RY];
+        real pr[NS], pim[NS], e1[NS], e2[NS], e3[NS];
 #pragma unroll
-        for (int m = 0; m < RY; ++m) {
-            const long long s = base + off[m];
-            pr[m] = v.pir[s]; pim[m] = v.pii[s];
-            e1[m] = v.e1[s]; e2[m] = v.e2[s]; e3[m] = v.e3[s];
+        for (int my = 0; my < RY; ++my) {
+            const long long s = base + roff[my];
+            IO::ld(v.pir + s, pr + my * RX);
+            IO::ld(v.pii + s, pim + my * RX);
+            IO::ld(v.e1 + s, e1 + my * RX);
+            IO::ld(v.e2 + s, e2 + my * RX);
+            IO::ld(v.e3 + s, e3 + my * RX);
         }
         // A: links and phi of plane z+1 from the prefetch, then prefetch z+2
         store_plane(bn);
-        cpx<real> ph_p[RY];
-        real th_p[RY][3];
+        cpx<real> ph_p[NS];
+        real th_p[NS][3];
 #pragma unroll
-        for (int m = 0; m < RY; ++m) {
+        for (int m = 0; m < NS; ++m) {
             ph_p[m] = { fph[m][0], fph[m][1] };
             th_p[m][0] = fth[m][0]; th_p[m][1] = fth[m][1]; th_p[m][2] = fth[m][2];
         }
@@ -180,14 +225,13 @@ __global__ void __launch_bounds__(256, MINB) k_fused(View<real> v, int N, int zc
 
         // B: plaquette sines of plane z on the tile (own sites) and its low halos
         const cpx<real> *U0 = sU + bc * 3 * NE, *U1p = sU + bn * 3 * NE;
-        real p12[RY], p13[RY], p23[RY];
+        real p12[NS], p13[NS], p23[NS];
 #pragma unroll
-        for (int m = 0; m < RY; ++m) {
-            const int e = eix[m];
+        for (int m = 0; m < NS; ++m) {
+            const int e = eix(m), p = pix(m);
             p12[m] = plaq(U0[e], U0[NE + e + 1], U0[e + EX], U0[NE + e]);
             p13[m] = plaq(U0[e], U0[2 * NE + e + 1], U1p[e], U0[2 * NE + e]);
             p23[m] = plaq(U0[NE + e], U0[2 * NE + e + EX], U1p[NE + e], U0[2 * NE + e]);
-            const int p = (wy + 8 * m + 1) * PX + lx + 1;
             sP[p] = p12[m];
             sP[G::NP + p] = p13[m];
             sP[2 * G::NP + p] = p23[m];
@@ -203,10 +247,10 @@ __global__ void __launch_bounds__(256, MINB) k_fused(View<real> v, int N, int zc
 
         // C: kicks and drifts of the own sites of plane z
         const cpx<real> *F0 = sF + bc * NE;
+        real o_pr[NS], o_pi[NS], o_e1[NS], o_e2[NS], o_e3[NS], o_fr[NS], o_fi[NS], o_t1[NS], o_t2[NS], o_t3[NS];
 #pragma unroll
-        for (int m = 0; m < RY; ++m) {
-            const int e = eix[m];
-            const int p = (wy + 8 * m + 1) * PX + lx + 1;
+        for (int m = 0; m < NS; ++m) {
+            const int e = eix(m), p = pix(m);
             const cpx<real> f0 = ph_0[m];
             const cpx<real> u1 = U0[e], u2 = U0[NE + e], u3 = U0[2 * NE + e];
             const cpx<real> u1m = U0[e - 1], u2m = U0[NE + e - EX], u3m = u3_m[m];
@@ -232,16 +276,13 @@ __global__ void __launch_bounds__(256, MINB) k_fused(View<real> v, int N, int zc
             const real ne1 = c.c_edamp * e1[m] + c.c_cur * cu1 - c.c_curl * cl1;
             const real ne2 = c.c_edamp * e2[m] + c.c_cur * cu2 - c.c_curl * cl2;
             const real ne3 = c.c_edamp * e3[m] + c.c_cur * cu3 - c.c_curl * cl3;
-            if (wr[m]) {
-                const long long s = base + off[m];
-                v.pir[s] = npr; v.pii[s] = npi;
-                v.e1[s] = ne1; v.e2[s] = ne2; v.e3[s] = ne3;
-                v.ophr[s] = f0.r + c.dt * npr;
-                v.ophi[s] = f0.i + c.dt * npi;
-                v.oth1[s] = th_0[m][0] + c.dt * ne1;
-                v.oth2[s] = th_0[m][1] + c.dt * ne2;
-                v.oth3[s] = th_0[m][2] + c.dt * ne3;
-            }
+            o_pr[m] = npr; o_pi[m] = npi;
+            o_e1[m] = ne1; o_e2[m] = ne2; o_e3[m] = ne3;
+            o_fr[m] = f0.r + c.dt * npr;
+            o_fi[m] = f0.i + c.dt * npi;
+            o_t1[m] = th_0[m][0] + c.dt * ne1;
+            o_t2[m] = th_0[m][1] + c.dt * ne2;
+            o_t3[m] = th_0[m][2] + c.dt * ne3;
             // march: plane z becomes z-1
             ph_m[m] = f0;
             u3_m[m] = u3;
@@ -250,28 +291,44 @@ __global__ void __launch_bounds__(256, MINB) k_fused(View<real> v, int N, int zc
             ph_0[m] = ph_p[m];
             th_0[m][0] = th_p[m][0]; th_0[m][1] = th_p[m][1]; th_0[m][2] = th_p[m][2];
         }
+#pragma unroll
+        for (int my = 0; my < RY; ++my) {
+            if (wr[my]) {
+                const long long s = base + roff[my];
+                const int k = my * RX;
+                IO::st(v.pir + s, o_pr + k); IO::st(v.pii + s, o_pi + k);
+                IO::st(v.e1 + s, o_e1 + k); IO::st(v.e2 + s, o_e2 + k); IO::st(v.e3 + s, o_e3 + k);
+                IO::st(v.ophr + s, o_fr + k); IO::st(v.ophi + s, o_fi + k);
+                IO::st(v.oth1 + s, o_t1 + k); IO::st(v.oth2 + s, o_t2 + k); IO::st(v.oth3 + s, o_t3 + k);
+            }
+        }
         __syncthreads();
     }
 }
 
-// Compile-time shapes of the fused step: tile height TY (32 x TY sites, 256
-// threads, TY/8 sites per thread) and the minimum number of resident CTAs per SM
-// the register allocation must allow.
-struct VariantInfo { int ty, minb, min_chunk; const char *name; };
+// Compile-time shapes of the fused step: tile height TY (TY/8 rows per thread),
+// RX sites per thread in x (tile width 32 RX; RX = 2 uses 8-byte vector
+// accesses and needs an even N), and the minimum resident CTAs per SM the
+// register allocation must allow; min_chunk is the shortest z chunk.
+struct VariantInfo { int ty, rx, minb, min_chunk; const char *name; };
 constexpr VariantInfo kVariants32[] = {
-    { 16, 2, 16, "ty16_b2" }, { 16, 3, 16, "ty16_b3" }, { 8, 4, 16, "ty8_b4" },
-    { 8, 3, 16, "ty8_b3" },  { 32, 1, 16, "ty32_b1" }, { 16, 2, 64, "ty16_b2_z64" },
+    { 16, 1, 2, 16, "ty16_b2" }, { 16, 1, 3, 16, "ty16_b3" }, { 8, 1, 4, 16, "ty8_b4" },
+    { 8, 1, 3, 16, "ty8_b3" },  { 32, 1, 1, 16, "ty32_b1" }, { 16, 1, 2, 64, "ty16_b2_z64" },
+    { 8, 2, 3, 16, "x2_ty8_b3" }, { 8, 2, 2, 16, "x2_ty8_b2" }, { 16, 2, 2, 16, "x2_ty16_b2" },
+    { 16, 2, 1, 16, "x2_ty16_b1" },
 };
-constexpr VariantInfo kVariants64[] = { { 16, 1, 16, "ty16_b1" }, { 8, 2, 16, "ty8_b2" } };
+constexpr VariantInfo kVariants64[] = { { 16, 1, 1, 16, "ty16_b1" }, { 8, 1, 2, 16, "ty8_b2" },
+                                        { 8, 2, 1, 16, "x2_ty8_b1" } };
 
-template <typename real, int TY, int MINB>
+template <typename real, int TY, int RX, int MINB>
 cudaError_t launch_shape(const View<real> &v, int N, const KickCoef<real> &c, int min_chunk, cudaStream_t st)
 {
-    using G = Geo<real, TY>;
+    using G = Geo<real, TY, RX>;
+    if (RX > 1 && (N & 1)) return cudaErrorInvalidValue;
     static bool configured = false;   // once per instantiation
     if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(k_fused<real, TY, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)G::smem);
+        cudaError_t e = cudaFuncSetAttribute(k_fused<real, TY, RX, MINB>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::smem);
         if (e != cudaSuccess) return e;
         configured = true;
     }
@@ -281,7 +338,7 @@ cudaError_t launch_shape(const View<real> &v, int N, const KickCoef<real> &c, in
     nch = max(1, min(nch, N / min_chunk));
     const int zc = (N + nch - 1) / nch;
     nch = (N + zc - 1) / zc;
-    k_fused<real, TY, MINB><<<dim3(tx, ty, nch), G::NT, G::smem, st>>>(v, N, zc, c);
+    k_fused<real, TY, RX, MINB><<<dim3(tx, ty, nch), G::NT, G::smem, st>>>(v, N, zc, c);
     return cudaGetLastError();
 }
 
@@ -297,17 +354,26 @@ template <>
 const char *fused_variant_name<double>(int k) { return kVariants64[k].name; }
 
 template <>
+bool fused_variant_ok<float>(int k, int N) { return kVariants32[k].rx == 1 || (N % 2 == 0); }
+template <>
+bool fused_variant_ok<double>(int k, int N) { return kVariants64[k].rx == 1 || (N % 2 == 0); }
+
+template <>
 cudaError_t launch_fused_step<float>(const View<float> &v, int N, const KickCoef<float> &c, int variant,
                                      cudaStream_t st)
 {
     const int mc = kVariants32[variant].min_chunk;
     switch (variant) {
-    case 0: return launch_shape<float, 16, 2>(v, N, c, mc, st);
-    case 1: return launch_shape<float, 16, 3>(v, N, c, mc, st);
-    case 2: return launch_shape<float, 8, 4>(v, N, c, mc, st);
-    case 3: return launch_shape<float, 8, 3>(v, N, c, mc, st);
-    case 4: return launch_shape<float, 32, 1>(v, N, c, mc, st);
-    case 5: return launch_shape<float, 16, 2>(v, N, c, mc, st);
+    case 0: return launch_shape<float, 16, 1, 2>(v, N, c, mc, st);
+    case 1: return launch_shape<float, 16, 1, 3>(v, N, c, mc, st);
+    case 2: return launch_shape<float, 8, 1, 4>(v, N, c, mc, st);
+    case 3: return launch_shape<float, 8, 1, 3>(v, N, c, mc, st);
+    case 4: return launch_shape<float, 32, 1, 1>(v, N, c, mc, st);
+    case 5: return launch_shape<float, 16, 1, 2>(v, N, c, mc, st);
+    case 6: return launch_shape<float, 8, 2, 3>(v, N, c, mc, st);
+    case 7: return launch_shape<float, 8, 2, 2>(v, N, c, mc, st);
+    case 8: return launch_shape<float, 16, 2, 2>(v, N, c, mc, st);
+    case 9: return launch_shape<float, 16, 2, 1>(v, N, c, mc, st);
     default: return cudaErrorInvalidValue;
     }
 }
@@ -317,8 +383,9 @@ cudaError_t launch_fused_step<double>(const View<double> &v, int N, const KickCo
 {
     const int mc = kVariants64[variant].min_chunk;
     switch (variant) {
-    case 0: return launch_shape<double, 16, 1>(v, N, c, mc, st);
-    case 1: return launch_shape<double, 8, 2>(v, N, c, mc, st);
+    case 0: return launch_shape<double, 16, 1, 1>(v, N, c, mc, st);
+    case 1: return launch_shape<double, 8, 1, 2>(v, N, c, mc, st);
+    case 2: return launch_shape<double, 8, 2, 1>(v, N, c, mc, st);
     default: return cudaErrorInvalidValue;
     }
 }

@@ -212,6 +212,49 @@ ah_status ah_set_variant(ah_sim *sim, int32_t variant);
  * (AH_ERR_BUSY otherwise).  Waits for the simulation's stream. */
 ah_status ah_autotune(ah_sim *sim, int32_t trial_steps, int32_t *chosen);
 
+/* Raw diagnostic sums as written by ah_observables_noalloc (208 bytes):
+ * sums[] in the order of ah_obs.sums, then max |G|, max |theta|, sum |W| by
+ * plaquette orientation (12, 13, 23), signed sums by orientation, the number of
+ * plaquettes with W != 0 and the number of non-finite sites. */
+typedef struct ah_sums {
+    double sums[16];
+    double gauss_max, max_abs_theta;
+    int64_t wind_abs_plane[3];
+    int64_t wind_plane[3];
+    int64_t n_pierced;
+    int64_t nonfinite;
+} ah_sums;
+
+/* Diagnostics of an FP32 state held in caller-owned device memory, with no
+ * device allocation of any kind.  The paper has no counterpart: this exists for
+ * callers that cannot call cudaMalloc -- a host framework that owns the whole
+ * device memory pool through its own allocator, loops that must not block on
+ * the driver's allocator once running, or a sandbox that forbids new device
+ * allocations after start-up.
+ *
+ *  fields   10 device pointers (component order above), each N^3 floats with x
+ *           fastest, 8-byte aligned; read only.
+ *  N, cfg   lattice side (must equal cfg->N; 4 <= N <= 2048) and the run's
+ *           configuration (cfg->precision must be AH_FP32; the couplings and
+ *           the scale factor at integer step `step` come from it).
+ *  d_sums   caller-owned device memory for one ah_sums (8-byte aligned),
+ *           written by the call.
+ *  stream   cudaStream_t (as void*) the work is enqueued on; the call returns
+ *           without waiting, so read d_sums after synchronising that stream.
+ * The per-site values and the sums are the same as those of ah_observables
+ * (fast path: FP32 energies, FP64 sums and Gauss residual, windings equal to the
+ * FP64 arctangent formula).  Scratch memory -- per-block partial sums and a list
+ * of at most 2^18 plaquettes near a branch cut -- lives in one static device
+ * array of 2.31 MB that every GPU which loads the library holds until exit; if
+ * a snapshot has more listed plaquettes than that, all windings of the call are
+ * recounted in FP64 (slower, same result).  The first call on a device looks up
+ * that array's address (a one-time set-up): make the first call before any
+ * stream capture.  All calls share the array, so calls whose work overlaps on
+ * the GPU (concurrent streams or threads) race and give wrong sums: serialise
+ * them.  Sizes out of range are rejected with AH_ERR_ARG. */
+ah_status ah_observables_noalloc(const float *const fields[10], int32_t N, const ah_config *cfg,
+                                 int64_t step, void *d_sums, void *cuda_stream);
+
 /* Free all resources of the simulation (NULL-safe). */
 void ah_destroy(ah_sim *sim);
 

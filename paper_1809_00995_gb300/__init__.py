@@ -95,6 +95,8 @@ _SIGS = {
     "ah_variant_count": ([ctypes.c_int32], ctypes.c_int32),
     "ah_set_variant": ([ctypes.c_void_p, ctypes.c_int32], ctypes.c_int),
     "ah_autotune": ([ctypes.c_void_p, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)], ctypes.c_int),
+    "ah_observables_noalloc": ([ctypes.POINTER(ctypes.c_void_p), ctypes.c_int32, ctypes.POINTER(ah_config),
+                                ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p], ctypes.c_int),
 }
 
 
@@ -228,6 +230,20 @@ def ah_autotune(h, trial_steps: int = 3) -> int:
 def ah_destroy(h):
     if h:
         load().ah_destroy(h)
+
+
+class ah_sums(ctypes.Structure):
+    _fields_ = [("sums", ctypes.c_double * 16), ("gauss_max", ctypes.c_double), ("max_abs_theta", ctypes.c_double),
+                ("wind_abs_plane", ctypes.c_int64 * 3), ("wind_plane", ctypes.c_int64 * 3),
+                ("n_pierced", ctypes.c_int64), ("nonfinite", ctypes.c_int64)]
+
+
+def ah_observables_noalloc(field_ptrs, N: int, cfg: ah_config, step: int, d_sums_ptr: int, stream_ptr=None):
+    """Diagnostics of an FP32 state in caller-owned device buffers (10 device
+    pointers), written as an ah_sums to the device pointer d_sums_ptr; no device
+    allocation.  Enqueued on stream_ptr; synchronise before reading the sums."""
+    arr = (ctypes.c_void_p * 10)(*[int(p) for p in field_ptrs])
+    _check(load().ah_observables_noalloc(arr, N, ctypes.byref(cfg), step, d_sums_ptr, stream_ptr or None))
 
 
 # ---- convenience ------------------------------------------------------------------

@@ -370,6 +370,12 @@ ah_status enter(const ah_sim *h)
 
 }  // namespace
 
+namespace ah {
+DiagCoef host_diag_coef(const ah_config &c, int64_t step) { return diag_coef(c, step); }
+ah_status host_validate(const ah_config &c) { return validate(c); }
+ah_status host_fail(ah_status st, const char *msg) { return fail(st, "%s", msg); }
+}  // namespace ah
+
 extern "C" {
 
 int ah_abi_version(void) { return 2; }

@@ -6,6 +6,8 @@
 #include <cuda.h>
 #include <cuda_runtime.h>
 
+#include "../../include/ah.h"
+
 namespace ah {
 
 // Device pointers of one state: 10 SoA arrays of N^3 reals (x fastest).
@@ -104,6 +106,11 @@ cudaError_t launch_diag(const View<real> &v, int N, Box b, const DiagCoef &c,
                         DiagList list, bool exact, cudaStream_t st);
 
 int diag_grid_blocks(int num_sms);
+
+// Host helpers of ah_api.cu shared with other translation units.
+DiagCoef host_diag_coef(const ah_config &c, int64_t step);
+ah_status host_validate(const ah_config &c);
+ah_status host_fail(ah_status st, const char *msg);
 
 // Fused step with paired FP32 arithmetic (N even), shapes 0..4.
 bool pair_shape_ok(int N);

@@ -30,6 +30,10 @@
 // shuffles; one block then adds the partials in index order, so the result
 // depends only on the launch shape, never on scheduling (integer atomics of the
 // fix-up are order independent).
+#include <algorithm>
+#include <cstdint>
+#include <mutex>
+
 #include "ah_internal.cuh"
 #include "sincos32.cuh"
 
@@ -475,4 +479,143 @@ template cudaError_t launch_diag<float>(const View<float> &, int, Box, const Dia
 template cudaError_t launch_diag<double>(const View<double> &, int, Box, const DiagCoef &, DiagPartial *, int,
                                          DiagPartial *, DiagList, bool, cudaStream_t);
 
+// ---------------------------------------------------------------------------
+// Diagnostics without any device allocation (ah_observables_noalloc).
+//
+// Some callers cannot call cudaMalloc: code that runs inside a host framework
+// that owns the whole device memory pool through its own allocator, loops that
+// must not block on the driver's allocator once they are running, and
+// processes whose sandbox forbids new device allocations after start-up.  This
+// entry point runs the fast diagnostics on an FP32 state held in the caller's
+// device buffers and keeps its own scratch -- the per-block partial sums and
+// the list of plaquettes near a branch cut -- in one file-scope device array
+// of fixed size, so it allocates nothing.
+namespace {
+
+constexpr int kNoAllocBlocks = 1024;                 // most per-block partials
+constexpr long long kNoAllocListCap = 1LL << 18;     // near-cut plaquettes listed
+constexpr size_t kNoAllocCountOff = sizeof(DiagPartial) * kNoAllocBlocks;
+constexpr size_t kNoAllocItemsOff = kNoAllocCountOff + 256;
+constexpr size_t kNoAllocBytes = kNoAllocItemsOff + sizeof(unsigned long long) * kNoAllocListCap;
+
+// 2.31 MB, held by every GPU that loads the library until the process exits.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+// Device addresses of g_noalloc_scratch, filled on the first call on each device.
+std::mutex g_noalloc_mu;
+void *g_noalloc_ptr[128] = {};
+
+// Windings of the listed plaquettes when the list did not overflow.
+template <typename real>
+__global__ void k_noalloc_fixup(View<real> v, int N, DiagList list, DiagPartial *result)
+{
+    const unsigned long long n = *list.count;
+    if (n > (unsigned long long)list.capacity) return;
+    const int I[3] = { 0, 0, 1 }, J[3] = { 1, 2, 2 };
+    for (unsigned long long k = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; k < n;
+         k += (unsigned long long)gridDim.x * blockDim.x) {
+        const unsigned long long item = list.items[k];
+        const int q = (int)(item & 3ULL);
+        const long long s = (long long)(item >> 2);
+        const int x = (int)(s % N), y = (int)((s / N) % N), z = (int)(s / ((long long)N * N));
+        const long long w = winding_fp64(v, N, I[q], J[q], x, y, z);
+        if (w) {
+            atomicAdd((unsigned long long *)&result->ints[q], (unsigned long long)(w < 0 ? -w : w));
+            atomicAdd((unsigned long long *)&result->ints[3 + q], (unsigned long long)w);
+            atomicAdd((unsigned long long *)&result->ints[6], 1ULL);
+        }
+    }
+}
+
+// On list overflow: clear the winding counters ...
+__global__ void k_noalloc_wind_clear(DiagList list, DiagPartial *result)
+{
+    if (*list.count <= (unsigned long long)list.capacity) return;
+    if (threadIdx.x < 7) result->ints[threadIdx.x] = 0;
+}
+
+// ... and count every plaquette of the lattice with the FP64 path.
+template <typename real>
+__global__ void k_noalloc_wind_all(View<real> v, int N, DiagList list, DiagPartial *result)
+{
+    if (*list.count <= (unsigned long long)list.capacity) return;
+    long long ic[7] = { 0, 0, 0, 0, 0, 0, 0 };
+    const long long ns = (long long)N * N * N;
+    const int I[3] = { 0, 0, 1 }, J[3] = { 1, 2, 2 };
+    for (long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x; s < ns; s += (long long)gridDim.x * blockDim.x) {
+        const int x = (int)(s % N), y = (int)((s / N) % N), z = (int)(s / ((long long)N * N));
+        for (int q = 0; q < 3; ++q) {
+            const long long w = winding_fp64(v, N, I[q], J[q], x, y, z);
+            ic[q] += w < 0 ? -w : w;
+            ic[3 + q] += w;
+            ic[6] += w != 0;
+        }
+    }
+    for (int k = 0; k < 7; ++k)
+        if (ic[k]) atomicAdd((unsigned long long *)&result->ints[k], (unsigned long long)ic[k]);
+}
+
+}  // namespace
+
 }  // namespace ah
+
+extern "C" ah_status ah_observables_noalloc(const float *const fields[10], int32_t N, const ah_config *cfg,
+                                            int64_t step, void *d_sums, void *cuda_stream)
+{
+    using namespace ah;
+    if (!fields || !cfg || !d_sums) return host_fail(AH_ERR_ARG, "ah_observables_noalloc: null argument");
+    if (N < 4 || N > 2048 || N != cfg->N)
+        return host_fail(AH_ERR_ARG, "ah_observables_noalloc: N must equal cfg->N and lie in [4, 2048]");
+    if (cfg->precision != AH_FP32)
+        return host_fail(AH_ERR_ARG, "ah_observables_noalloc: the fields must be an FP32 state (cfg->precision)");
+    if (step < 0) return host_fail(AH_ERR_ARG, "ah_observables_noalloc: step must be >= 0");
+    for (int k = 0; k < 10; ++k)
+        if (!fields[k] || (reinterpret_cast<uintptr_t>(fields[k]) & 7))
+            return host_fail(AH_ERR_ARG, "ah_observables_noalloc: field pointers must be non-null and 8-byte aligned");
+    if (reinterpret_cast<uintptr_t>(d_sums) & 7)
+        return host_fail(AH_ERR_ARG, "ah_observables_noalloc: d_sums must be 8-byte aligned");
+    ah_status st = host_validate(*cfg);
+    if (st != AH_OK) return st;
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 128 ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return host_fail(AH_ERR_CUDA, "ah_observables_noalloc: no usable CUDA device");
+    void *base = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(g_noalloc_mu);
+        if (!g_noalloc_ptr[dev]) {
+            void *p = nullptr;
+            const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+            if (e != cudaSuccess || !p)
+                return host_fail(AH_ERR_CUDA, "ah_observables_noalloc: cudaGetSymbolAddress of the scratch failed");
+            g_noalloc_ptr[dev] = p;
+        }
+        base = g_noalloc_ptr[dev];
+    }
+    cudaStream_t stream = (cudaStream_t)cuda_stream;
+    View<float> v{};
+    v.phr = fields[0]; v.phi = fields[1];
+    v.pir = const_cast<float *>(fields[2]); v.pii = const_cast<float *>(fields[3]);
+    v.th1 = fields[4]; v.th2 = fields[5]; v.th3 = fields[6];
+    v.e1 = const_cast<float *>(fields[7]); v.e2 = const_cast<float *>(fields[8]); v.e3 = const_cast<float *>(fields[9]);
+    DiagPartial *partials = reinterpret_cast<DiagPartial *>(base);
+    DiagList list;
+    list.count = reinterpret_cast<unsigned long long *>(static_cast<char *>(base) + kNoAllocCountOff);
+    list.items = reinterpret_cast<unsigned long long *>(static_cast<char *>(base) + kNoAllocItemsOff);
+    list.capacity = kNoAllocListCap;
+    DiagPartial *result = reinterpret_cast<DiagPartial *>(d_sums);
+    const int nblocks = std::min(diag_grid_blocks(sms), kNoAllocBlocks);
+    const Box b{ 0, 0, 0, N, N, N };
+    const DiagCoef dc = host_diag_coef(*cfg, step);
+    cudaError_t e = cudaMemsetAsync(list.count, 0, sizeof(unsigned long long), stream);
+    if (e == cudaSuccess) {
+        k_diag_fast<float><<<nblocks, NT, 0, stream>>>(v, N, b, dc, partials, list);
+        k_diag_finish<<<1, 32, 0, stream>>>(partials, nblocks, result);
+        k_noalloc_fixup<float><<<nblocks, 128, 0, stream>>>(v, N, list, result);
+        k_noalloc_wind_clear<<<1, 32, 0, stream>>>(list, result);
+        k_noalloc_wind_all<float><<<nblocks, 256, 0, stream>>>(v, N, list, result);
+        e = cudaGetLastError();
+    }
+    if (e != cudaSuccess) return host_fail(AH_ERR_CUDA, cudaGetErrorString(e));
+    return AH_OK;
+}

@@ -272,6 +272,8 @@ ah_status check_device_error(ah_sim *h)
     return AH_OK;
 }
 
+void fill_obs(const ah_config &c, int64_t step, int64_t n_sites, const DiagPartial &r, ah_obs *out);
+
 template <typename real>
 ah_status do_diag(ah_sim *h, Box b, ah_obs *out)
 {
@@ -296,14 +298,21 @@ ah_status do_diag(ah_sim *h, Box b, ah_obs *out)
                                 h->stream));
         AH_CUDA(cudaStreamSynchronize(h->stream));
     }
-    const DiagPartial &r = *h->host_result;
-    const ah_config &c = h->cfg;
+    fill_obs(h->cfg, h->step, (int64_t)b.nx * b.ny * b.nz, *h->host_result, out);
+    if (out->nonfinite)
+        return fail(AH_ERR_NONFINITE, "%lld sites have non-finite diagnostics", (long long)out->nonfinite);
+    return AH_OK;
+}
+
+// Observables (Eqs. defXiV2, defR, 9, defEoS, Gauss residual) from the raw sums.
+void fill_obs(const ah_config &c, int64_t step, int64_t n_sites, const DiagPartial &r, ah_obs *out)
+{
     ah_obs o;
     memset(&o, 0, sizeof o);
-    o.step = h->step;
-    o.tau = tau_of(c, h->step);
+    o.step = step;
+    o.tau = tau_of(c, step);
     o.a = scale_factor(c, o.tau);
-    o.n_sites = (int64_t)b.nx * b.ny * b.nz;
+    o.n_sites = n_sites;
     for (int k = 0; k < kNumSums; ++k) o.sums[k] = r.sums[k];
     for (int q = 0; q < 3; ++q) {
         o.wind_abs_plane[q] = r.ints[q];
@@ -328,8 +337,6 @@ ah_status do_diag(ah_sim *h, Box b, ah_obs *out)
     o.energy = c.dx * c.dx * c.dx * o.sums[1];
     o.max_abs_theta = r.maxv[1];
     *out = o;
-    if (o.nonfinite) return fail(AH_ERR_NONFINITE, "%lld sites have non-finite diagnostics", (long long)o.nonfinite);
-    return AH_OK;
 }
 
 // Random-phase initial state (Sec. 2): zero everything, then phi of buffer 0.
@@ -371,6 +378,14 @@ ah_status enter(const ah_sim *h)
 }  // namespace
 
 namespace ah {
+KickCoef<float> host_kick_coef32(const ah_config &c, int64_t step) { return kick_coef<float>(c, step); }
+void host_carve32(Fields<float> &F, void *base, size_t nsites) { carve(F, (char *)base, nsites); }
+size_t host_state_bytes32(size_t nsites) { return 15 * padded(nsites) * sizeof(float); }
+void host_fill_obs(const ah_config &c, int64_t step, int64_t n_sites, const DiagPartial &r, ah_obs *out)
+{
+    fill_obs(c, step, n_sites, r, out);
+}
+int64_t host_run_steps(const ah_config &c) { return (int64_t)std::llround((c.tau_end - c.tau0) / c.dt); }
 DiagCoef host_diag_coef(const ah_config &c, int64_t step) { return diag_coef(c, step); }
 ah_status host_validate(const ah_config &c) { return validate(c); }
 ah_status host_fail(ah_status st, const char *msg) { return fail(st, "%s", msg); }

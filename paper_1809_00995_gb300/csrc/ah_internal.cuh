@@ -108,9 +108,29 @@ cudaError_t launch_diag(const View<real> &v, int N, Box b, const DiagCoef &c,
 int diag_grid_blocks(int num_sms);
 
 // Host helpers of ah_api.cu shared with other translation units.
+KickCoef<float> host_kick_coef32(const ah_config &c, int64_t step);
+void host_carve32(Fields<float> &F, void *base, size_t nsites);
+size_t host_state_bytes32(size_t nsites);
+void host_fill_obs(const ah_config &c, int64_t step, int64_t n_sites, const DiagPartial &r, ah_obs *out);
+int64_t host_run_steps(const ah_config &c);    // round((tau_end - tau0) / dt)
 DiagCoef host_diag_coef(const ah_config &c, int64_t step);
 ah_status host_validate(const ah_config &c);
 ah_status host_fail(ah_status st, const char *msg);
+
+// Batched fused step (FP32): one descriptor per lattice, work items (lattice,
+// tile index), device-side step counters.
+struct BatchLattice {
+    Fields<float> F;
+    int N, zc, tiles_x, tiles_y, nchunk;
+    int nsteps;                      // steps this lattice runs in total
+    const KickCoef<float> *coefs;    // [nsteps] coefficients of each step
+};
+struct BatchState { int step; int cur; };
+int batch_shape_count();
+bool batch_shape_ok(int shape, int N);
+void batch_tiles(int shape, int N, int *tx, int *ty);
+cudaError_t launch_fused_batch(int shape, const BatchLattice *lat, BatchState *state, int nlat, const int2 *items,
+                               const int *nitems, unsigned int *counter, int num_sms, cudaStream_t st);
 
 // Fused step with paired FP32 arithmetic (N even), shapes 0..4.
 bool pair_shape_ok(int N);

@@ -78,20 +78,21 @@ template <> struct Row<double, 2> {
 };
 
 // Each thread owns RX consecutive sites in x times RY rows (y stride 8).
-template <typename real, int TY, int RX, int MINB>
-__global__ void __launch_bounds__(256, MINB) k_fused(View<real> v, int N, int zc, KickCoef<real> c)
+// One work item of the fused step: tile (bx, by) of plane chunk bz, marched in z.
+template <typename real, int TY, int RX>
+__device__ __forceinline__ void fused_tile(const View<real> &v, int N, int zc, const KickCoef<real> &c,
+                                           int bx, int by, int bz, unsigned char *smem_raw)
 {
     using G = Geo<real, TY, RX>;
     using IO = Row<real, RX>;
     constexpr int TX = G::TX, RY = G::RY, NS = G::NS, EX = G::EX, EY = G::EY, NE = G::NE, PX = G::PX;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
     cpx<real> *sU = reinterpret_cast<cpx<real> *>(smem_raw);   // [2 planes][3 dirs][NE]
     cpx<real> *sF = sU + 2 * 3 * NE;                            // [2 planes][NE] phi
     real *sP = reinterpret_cast<real *>(sF + 2 * NE);           // [3][NP] sin Xi_12, _13, _23
 
     const int tid = threadIdx.x, lx = tid & 31, wy = tid >> 5;
-    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
-    const int z0 = blockIdx.z * zc;
+    const int x0 = bx * TX, y0 = by * TY;
+    const int z0 = bz * zc;
     if (z0 >= N) return;
     const int z1 = min(z0 + zc, N);
     const long long NN = (long long)N * N;
@@ -306,6 +307,63 @@ __global__ void __launch_bounds__(256, MINB) k_fused(View<real> v, int N, int zc
     }
 }
 
+template <typename real, int TY, int RX, int MINB>
+__global__ void __launch_bounds__(256, MINB) k_fused(View<real> v, int N, int zc, KickCoef<real> c)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    fused_tile<real, TY, RX>(v, N, zc, c, blockIdx.x, blockIdx.y, blockIdx.z, smem_raw);
+}
+
+// Batched fused step: persistent CTAs take (lattice, tile) work items from a
+// shared counter and advance every lattice of the batch by one step.  Lattices
+// that have run all their steps are skipped; each lattice's step number, read
+// buffer and coefficient table live in device memory (advanced by
+// k_batch_advance), so the same launch sequence can be replayed from a graph.
+template <int TY, int RX, int MINB>
+__global__ void __launch_bounds__(256, MINB)
+k_fused_batch(const BatchLattice *lat, BatchState *state, const int2 *items, const int *nitems,
+              unsigned int *counter)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ int s_item;
+    const int n = *nitems;
+    for (;;) {
+        if (threadIdx.x == 0) s_item = (int)atomicAdd(counter, 1u);
+        __syncthreads();
+        const int it = s_item;
+        __syncthreads();
+        if (it >= n) break;
+        const int L = items[it].x, local = items[it].y;
+        const BatchLattice &B = lat[L];
+        const int step = state[L].step;
+        if (step >= B.nsteps) continue;
+        const int cur = state[L].cur, o = 1 - cur;
+        View<float> v;
+        v.phr = B.F.phr[cur]; v.phi = B.F.phi[cur];
+        v.th1 = B.F.th[cur][0]; v.th2 = B.F.th[cur][1]; v.th3 = B.F.th[cur][2];
+        v.pir = B.F.pir; v.pii = B.F.pii;
+        v.e1 = B.F.el[0]; v.e2 = B.F.el[1]; v.e3 = B.F.el[2];
+        v.ophr = B.F.phr[o]; v.ophi = B.F.phi[o];
+        v.oth1 = B.F.th[o][0]; v.oth2 = B.F.th[o][1]; v.oth3 = B.F.th[o][2];
+        const int bx = local % B.tiles_x, by = (local / B.tiles_x) % B.tiles_y, bz = local / (B.tiles_x * B.tiles_y);
+        fused_tile<float, TY, RX>(v, B.N, B.zc, B.coefs[step], bx, by, bz, smem_raw);
+        __syncthreads();
+    }
+}
+
+// After a batched step: every unfinished lattice moves to its next step and
+// swaps its phi/theta buffers; the work counter is reset.
+__global__ void k_batch_advance(const BatchLattice *lat, BatchState *state, int nlat, unsigned int *counter)
+{
+    for (int L = threadIdx.x; L < nlat; L += blockDim.x) {
+        if (state[L].step < lat[L].nsteps) {
+            state[L].step += 1;
+            state[L].cur ^= 1;
+        }
+    }
+    if (threadIdx.x == 0) *counter = 0u;
+}
+
 // Compile-time shapes of the fused step: tile height TY (TY/8 rows per thread),
 // RX sites per thread in x (tile width 32 RX; RX = 2 uses 8-byte vector
 // accesses and needs an even N), and the minimum resident CTAs per SM the
@@ -386,6 +444,54 @@ cudaError_t launch_fused_step<double>(const View<double> &v, int N, const KickCo
     case 0: return launch_shape<double, 16, 1, 1>(v, N, c, mc, st);
     case 1: return launch_shape<double, 8, 1, 2>(v, N, c, mc, st);
     case 2: return launch_shape<double, 8, 2, 1>(v, N, c, mc, st);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+
+// ---- batched step ----
+namespace {
+struct BatchShape { int ty, rx, minb; };
+constexpr BatchShape kBatchShapes[] = { { 8, 1, 4 }, { 16, 1, 2 }, { 8, 2, 2 } };
+
+template <int TY, int RX, int MINB>
+cudaError_t launch_batch_shape(const BatchLattice *lat, BatchState *state, int nlat, const int2 *items,
+                               const int *nitems, unsigned int *counter, int num_sms, cudaStream_t st)
+{
+    using G = Geo<float, TY, RX>;
+    static int blocks_per_sm = 0;
+    if (!blocks_per_sm) {
+        cudaError_t e = cudaFuncSetAttribute(k_fused_batch<TY, RX, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)G::smem);
+        if (e != cudaSuccess) return e;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, k_fused_batch<TY, RX, MINB>, 256, G::smem);
+        if (e != cudaSuccess) return e;
+        if (blocks_per_sm < 1) blocks_per_sm = 1;
+    }
+    k_fused_batch<TY, RX, MINB><<<num_sms * blocks_per_sm, 256, G::smem, st>>>(lat, state, items, nitems, counter);
+    k_batch_advance<<<1, 256, 0, st>>>(lat, state, nlat, counter);
+    return cudaGetLastError();
+}
+}  // namespace
+
+int batch_shape_count() { return (int)(sizeof(kBatchShapes) / sizeof(kBatchShapes[0])); }
+
+void batch_tiles(int shape, int N, int *tx, int *ty)
+{
+    const BatchShape &b = kBatchShapes[shape];
+    *tx = (N + 32 * b.rx - 1) / (32 * b.rx);
+    *ty = (N + b.ty - 1) / b.ty;
+}
+
+bool batch_shape_ok(int shape, int N) { return kBatchShapes[shape].rx == 1 || N % 2 == 0; }
+
+cudaError_t launch_fused_batch(int shape, const BatchLattice *lat, BatchState *state, int nlat, const int2 *items,
+                               const int *nitems, unsigned int *counter, int num_sms, cudaStream_t st)
+{
+    switch (shape) {
+    case 0: return launch_batch_shape<8, 1, 4>(lat, state, nlat, items, nitems, counter, num_sms, st);
+    case 1: return launch_batch_shape<16, 1, 2>(lat, state, nlat, items, nitems, counter, num_sms, st);
+    case 2: return launch_batch_shape<8, 2, 2>(lat, state, nlat, items, nitems, counter, num_sms, st);
     default: return cudaErrorInvalidValue;
     }
 }

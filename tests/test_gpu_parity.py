@@ -305,3 +305,50 @@ def test_stepping_is_deterministic():
             outs.append((g.fields(), g.observables()["sums"]))
     assert np.array_equal(outs[0][0], outs[1][0])
     assert outs[0][1] == outs[1][1]
+
+
+# ------------------------------------------------------------------ full-size cases
+@pytest.mark.parametrize("precision", [ah.AH_FP64, ah.AH_FP32])
+def test_256cubed_first_20_steps_match_oracle(precision):
+    """256^3, radiation era, s = 0, seed 2: all fields of the whole lattice after 20
+    steps, the oracle run from the GPU's initial snapshot."""
+    N = 256
+    p = oparams(N, ah.AH_RADIATION, 0.0, seed=2)
+    with sim(N, precision, ah.AH_KERNEL_FUSED, ah.AH_RADIATION, 0.0, seed=2, flags=ah.AH_FLAG_AUTOTUNE) as g:
+        f0 = g.fields()
+        g.step(20)
+        got = g.fields()
+        go = g.observables()
+    ref = O.evolve(p, f0, 0, 20)
+    assert max(rel_err(got, ref)) <= TOL[precision]
+    compare_obs(go, O.observables(p, got, 20), precision)
+    del ref, got, f0
+
+
+def test_1024cubed_fp32_light_cone_windows():
+    """1024^3 FP32, matter era, s = 1, seed 3, in the bench's launch configuration
+    (autotuned shape): after 20 steps the fields in three 16^3 windows (two across
+    the periodic seam) equal the oracle's evolution of (16 + 2*20)^3 windows of the
+    same initial lattice; diagnostics of sub-boxes match the oracle on fetched
+    windows; the Gauss residual stays at FP32 roundoff over the whole lattice."""
+    N, k, b = 1024, 20, 16
+    p = oparams(N, ah.AH_MATTER, 1.0, seed=3)
+    with sim(N, ah.AH_FP32, ah.AH_KERNEL_FUSED, ah.AH_MATTER, 1.0, seed=3, flags=ah.AH_FLAG_AUTOTUNE) as g:
+        g.step(k)
+        for org in [(1016, 5, 1019), (300, 1010, 7), (511, 512, 640)]:
+            M = b + 2 * k
+            w0 = [(o - k) % N for o in org]
+            win = O.init(p, M=M, origin=w0)
+            win32 = win.astype(np.float32).astype(np.float64)      # the FP32 state's initial values
+            O.evolve(p, win32, 0, k)
+            got = g.fields(*org, b, b, b)
+            ref = win32[:, k:k + b, k:k + b, k:k + b]
+            assert max(rel_err(got, ref)) <= TOL[ah.AH_FP32], org
+            # diagnostics of the b^3 box against the oracle on a (b+2)^3 fetched window
+            fw = g.fields(*[(o - 1) % N for o in org], b + 2, b + 2, b + 2)
+            go = g.observables_box(*org, b, b, b)
+            oo = O.observables(p, fw, k, box=(1, 1, 1, b, b, b))
+            compare_obs(go, oo, ah.AH_FP32)
+        o = g.observables()
+    assert o["n_sites"] == N ** 3 and o["nonfinite"] == 0
+    assert o["gauss_rel"] < 1e-5

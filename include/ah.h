@@ -212,6 +212,68 @@ ah_status ah_set_variant(ah_sim *sim, int32_t variant);
  * (AH_ERR_BUSY otherwise).  Waits for the simulation's stream. */
 ah_status ah_autotune(ah_sim *sim, int32_t trial_steps, int32_t *chosen);
 
+/* ---- batched ensembles (the ensembles of independent runs of Sec. 4) ----
+ *
+ * Many independent FP32 lattices (any mix of N, era, s, seed) advance together:
+ * one persistent kernel launch per leapfrog step covers every resident lattice
+ * (work items = lattice tiles), each lattice with its own coefficient table and
+ * step counter on the device; the steps between diagnostic points are replayed
+ * from a CUDA graph.  Every lattice computes exactly what ah_step computes for
+ * it alone. */
+enum { AH_BATCH_AUTOTUNE = 1, AH_BATCH_NO_GRAPH = 2 };
+
+typedef struct ah_batch_stats {
+    double seconds;          /* wall time of the evolution and diagnostics       */
+    double setup_seconds;    /* allocation, initial states, shape tuning         */
+    double site_updates;     /* sum over lattices of N^3 x steps                 */
+    double sims_per_hour;    /* count x 3600 / seconds                           */
+    int32_t shape;           /* batched-kernel shape used                        */
+    int32_t rounds;          /* graph (or launch-sequence) replays               */
+    int64_t launches;        /* kernel launches of the batched steps             */
+} ah_batch_stats;
+
+/* Run `count` lattices (cfgs[i]: precision AH_FP32; each runs
+ * round((tau_end - tau0)/dt) steps) to their ends.  If series is not NULL it
+ * holds count x series_cap ah_obs (lattice-major): for lattice i, observables at
+ * step 0, every cfgs[i].diag_every steps (if > 0) and at the end;
+ * series_len[i] receives the number produced (entries past series_cap are
+ * dropped).  flags: AH_BATCH_AUTOTUNE (time each batched shape on the initial
+ * states, then restore them), AH_BATCH_NO_GRAPH (plain launches).  stats may be
+ * NULL.  Synchronous; all device memory is released before return. */
+ah_status ah_batch_run(const ah_config *cfgs, int32_t count, int32_t flags, ah_obs *series,
+                       int64_t series_cap, int64_t *series_len, ah_batch_stats *stats);
+
+/* ---- continuous-batching server ----
+ *
+ * A scheduler thread admits submitted requests (FIFO) whenever a slot is free
+ * and the request's device memory fits the HBM budget, keeps every admitted
+ * lattice resident, advances all of them together with the batched step in
+ * rounds of at most 20 steps (so newly admitted work joins within a round), and
+ * retires each lattice at its tau_end with its final observables.  Times are in
+ * seconds since the server was created. */
+typedef struct ah_server ah_server;
+typedef struct ah_server_stats {
+    int64_t submitted, admitted, completed;
+    int32_t running, queued;
+    int64_t hbm_used;        /* bytes held by resident lattices                  */
+    double site_updates;     /* total site-updates performed                     */
+    int64_t launches;        /* kernel launches of the batched steps             */
+} ah_server_stats;
+
+/* Start a server on the current device.  flags: 0 or AH_BATCH_NO_GRAPH. */
+ah_status ah_server_create(size_t hbm_budget_bytes, int32_t max_slots, int32_t flags, ah_server **out);
+/* Queue one run (precision AH_FP32); AH_ERR_OOM if it can never fit the budget. */
+ah_status ah_server_submit(ah_server *srv, const ah_config *cfg, uint64_t *req_id);
+/* AH_OK with the final observables and times once done; AH_ERR_BUSY while queued
+ * or running; AH_ERR_CANCELLED, AH_ERR_NOTFOUND, AH_ERR_CUDA (failed run). */
+ah_status ah_server_poll(ah_server *srv, uint64_t req_id, ah_obs *final_out, double *t_submit,
+                         double *t_done);
+/* Drop a queued or running request (its memory is released by the scheduler). */
+ah_status ah_server_cancel(ah_server *srv, uint64_t req_id);
+ah_status ah_server_stats_get(ah_server *srv, ah_server_stats *out);
+/* Stop the scheduler (running requests are abandoned) and free everything. */
+void ah_server_destroy(ah_server *srv);
+
 /* Raw diagnostic sums as written by ah_observables_noalloc (208 bytes):
  * sums[] in the order of ah_obs.sums, then max |G|, max |theta|, sum |W| by
  * plaquette orientation (12, 13, 23), signed sums by orientation, the number of

@@ -27,6 +27,7 @@ AH_MINKOWSKI, AH_RADIATION, AH_MATTER = 0, 1, 2
 AH_FP32, AH_FP64 = 0, 1
 AH_KERNEL_AUTO, AH_KERNEL_PLAIN, AH_KERNEL_FUSED = 0, 1, 2
 AH_FLAG_EXACT_DIAG, AH_FLAG_AUTOTUNE = 1, 2
+AH_BATCH_AUTOTUNE, AH_BATCH_NO_GRAPH = 1, 2
 
 SUM_NAMES = ("L", "rho", "p", "K", "G2", "V", "Eel", "B", "KV", "G2V", "KL", "G2L", "pL", "rhoL",
              "gauss2", "gscale2")
@@ -67,6 +68,18 @@ class ah_obs(ctypes.Structure):
         return d
 
 
+class ah_batch_stats(ctypes.Structure):
+    _fields_ = [("seconds", ctypes.c_double), ("setup_seconds", ctypes.c_double), ("site_updates", ctypes.c_double),
+                ("sims_per_hour", ctypes.c_double), ("shape", ctypes.c_int32), ("rounds", ctypes.c_int32),
+                ("launches", ctypes.c_int64)]
+
+
+class ah_server_stats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_int64), ("admitted", ctypes.c_int64), ("completed", ctypes.c_int64),
+                ("running", ctypes.c_int32), ("queued", ctypes.c_int32), ("hbm_used", ctypes.c_int64),
+                ("site_updates", ctypes.c_double), ("launches", ctypes.c_int64)]
+
+
 class ah_info(ctypes.Structure):
     _fields_ = [("N", ctypes.c_int64), ("n_sites", ctypes.c_int64), ("precision", ctypes.c_int32),
                 ("kernel", ctypes.c_int32), ("state_bytes", ctypes.c_int64), ("step_bytes", ctypes.c_int64),
@@ -97,6 +110,16 @@ _SIGS = {
     "ah_autotune": ([ctypes.c_void_p, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)], ctypes.c_int),
     "ah_observables_noalloc": ([ctypes.POINTER(ctypes.c_void_p), ctypes.c_int32, ctypes.POINTER(ah_config),
                                 ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p], ctypes.c_int),
+    "ah_batch_run": ([ctypes.POINTER(ah_config), ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(ah_obs),
+                      ctypes.c_int64, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ah_batch_stats)], ctypes.c_int),
+    "ah_server_create": ([ctypes.c_size_t, ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(ctypes.c_void_p)],
+                         ctypes.c_int),
+    "ah_server_submit": ([ctypes.c_void_p, ctypes.POINTER(ah_config), ctypes.POINTER(ctypes.c_uint64)], ctypes.c_int),
+    "ah_server_poll": ([ctypes.c_void_p, ctypes.c_uint64, ctypes.POINTER(ah_obs), ctypes.POINTER(ctypes.c_double),
+                        ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
+    "ah_server_cancel": ([ctypes.c_void_p, ctypes.c_uint64], ctypes.c_int),
+    "ah_server_stats_get": ([ctypes.c_void_p, ctypes.POINTER(ah_server_stats)], ctypes.c_int),
+    "ah_server_destroy": ([ctypes.c_void_p], None),
 }
 
 
@@ -244,6 +267,61 @@ def ah_observables_noalloc(field_ptrs, N: int, cfg: ah_config, step: int, d_sums
     allocation.  Enqueued on stream_ptr; synchronise before reading the sums."""
     arr = (ctypes.c_void_p * 10)(*[int(p) for p in field_ptrs])
     _check(load().ah_observables_noalloc(arr, N, ctypes.byref(cfg), step, d_sums_ptr, stream_ptr or None))
+
+
+def ah_batch_run(cfgs, flags: int = 0, series_cap: int = 64):
+    """Run a batch of FP32 lattices to their ends; returns (series, stats): series[i]
+    is the list of observable dicts of lattice i (step 0, every diag_every, end)."""
+    n = len(cfgs)
+    arr = (ah_config * n)(*cfgs)
+    series = (ah_obs * (n * series_cap))()
+    lens = (ctypes.c_int64 * n)()
+    st = ah_batch_stats()
+    _check(load().ah_batch_run(arr, n, flags, series, series_cap, lens, ctypes.byref(st)))
+    out = [[series[i * series_cap + k].as_dict() for k in range(min(lens[i], series_cap))] for i in range(n)]
+    return out, {k: getattr(st, k) for k, _ in st._fields_}
+
+
+class Server:
+    """Continuous-batching server (ah_server_*): submit runs, poll their results."""
+
+    def __init__(self, hbm_budget_bytes: int, max_slots: int = 64, flags: int = 0):
+        h = ctypes.c_void_p()
+        _check(load().ah_server_create(hbm_budget_bytes, max_slots, flags, ctypes.byref(h)))
+        self.h = h.value
+
+    def submit(self, cfg: ah_config) -> int:
+        rid = ctypes.c_uint64()
+        _check(load().ah_server_submit(self.h, ctypes.byref(cfg), ctypes.byref(rid)))
+        return rid.value
+
+    def poll(self, rid: int):
+        """None while queued or running, else (obs dict, t_submit, t_done)."""
+        o, ts, td = ah_obs(), ctypes.c_double(), ctypes.c_double()
+        st = load().ah_server_poll(self.h, rid, ctypes.byref(o), ctypes.byref(ts), ctypes.byref(td))
+        if st == AH_ERR_BUSY:
+            return None
+        _check(st)
+        return o.as_dict(), ts.value, td.value
+
+    def cancel(self, rid: int):
+        _check(load().ah_server_cancel(self.h, rid))
+
+    def stats(self) -> dict:
+        s = ah_server_stats()
+        _check(load().ah_server_stats_get(self.h, ctypes.byref(s)))
+        return {k: getattr(s, k) for k, _ in s._fields_}
+
+    def close(self):
+        if self.h:
+            load().ah_server_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
 
 
 # ---- convenience ------------------------------------------------------------------

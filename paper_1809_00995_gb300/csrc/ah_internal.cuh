@@ -129,6 +129,7 @@ struct BatchState { int step; int cur; };
 int batch_shape_count();
 bool batch_shape_ok(int shape, int N);
 void batch_tiles(int shape, int N, int *tx, int *ty);
+cudaError_t batch_shape_prepare(int shape, int num_sms, cudaStream_t st);
 cudaError_t launch_fused_batch(int shape, const BatchLattice *lat, BatchState *state, int nlat, const int2 *items,
                                const int *nitems, unsigned int *counter, int num_sms, cudaStream_t st);
 

@@ -476,6 +476,25 @@ cudaError_t launch_batch_shape(const BatchLattice *lat, BatchState *state, int n
 
 int batch_shape_count() { return (int)(sizeof(kBatchShapes) / sizeof(kBatchShapes[0])); }
 
+// Per-shape one-time set-up (shared-memory attribute, occupancy) done outside
+// any stream capture: a launch of an empty work list.
+cudaError_t batch_shape_prepare(int shape, int num_sms, cudaStream_t st)
+{
+    static BatchState *d_dummy = nullptr;
+    static int *d_zero = nullptr;
+    static unsigned int *d_cnt = nullptr;
+    if (!d_dummy) {
+        cudaError_t e = cudaMalloc(&d_dummy, sizeof(BatchState));
+        if (e == cudaSuccess) e = cudaMalloc(&d_zero, sizeof(int));
+        if (e == cudaSuccess) e = cudaMalloc(&d_cnt, sizeof(unsigned int));
+        if (e == cudaSuccess) e = cudaMemsetAsync(d_zero, 0, sizeof(int), st);
+        if (e == cudaSuccess) e = cudaMemsetAsync(d_cnt, 0, sizeof(unsigned int), st);
+        if (e != cudaSuccess) return e;
+    }
+    // nlat = 0: the advance kernel touches no lattice; nitems = 0: no work
+    return launch_fused_batch(shape, nullptr, d_dummy, 0, nullptr, d_zero, d_cnt, num_sms, st);
+}
+
 void batch_tiles(int shape, int N, int *tx, int *ty)
 {
     const BatchShape &b = kBatchShapes[shape];

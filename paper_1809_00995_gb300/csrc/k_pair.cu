@@ -105,7 +105,7 @@ __global__ void __launch_bounds__(32 * (TY + 2), MINB)
 k_pair(View<float> v, int N, int zc, KickCoef<float> c)
 {
     using G = PGeo<TY>;
-    constexpr int EY = G::EY, ROWS = G::ROWS, PLANE = G::PLANE, PROWS = G::PROWS;
+    constexpr int ROWS = G::ROWS, PLANE = G::PLANE, PROWS = G::PROWS;
     extern __shared__ __align__(16) float sm[];
     float *const ring = sm;                     // [3][PLANE]
     float *const sP = sm + 3 * PLANE;           // [3][PROWS]: sin Xi_12, _13, _23

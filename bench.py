@@ -46,6 +46,7 @@ WORKLOADS = {
 DEFAULT = "lattice1024_fp32_matter_s1"
 BYTES_PER_SITE = {0: 80, 1: 160}      # one read + one write of the 10-real state
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "fused_step_traffic.json")
+TRAFFIC_VARIANT = "ty16_b2"           # shape the committed DRAM-traffic capture was taken on
 
 
 def parse():
@@ -57,6 +58,10 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-plain", action="store_true", help="skip the plain FP64 comparison run")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
+    ap.add_argument("--no-batch", action="store_true", help="skip the batched-ensemble measurement")
+    ap.add_argument("--no-serve", action="store_true", help="skip the serving measurement")
+    ap.add_argument("--serve-requests", type=int, default=40,
+                    help="requests of the serving run (500 for the full workload; 2 per second)")
     return ap.parse_args()
 
 
@@ -158,6 +163,99 @@ def cpu_oracle_rate(wl, budget_s=12.0, M=48):
                         "(%.2f s) weighted 1/%d" % (M, N, n, t_step, t_diag, diag_every)
 
 
+def batch_configs(ah, count=64, seed=4):
+    """The batched-ensemble workload: N ~ U{64, 96, 128, 192, 256}, era ~ U{radiation,
+    matter}, s ~ U{0, 1} from a fixed-seed host RNG, seeds 100..163, each run to
+    tau = N dx / 2 (FP32)."""
+    import numpy as np
+    rng = np.random.Generator(np.random.PCG64(seed))
+    cfgs = []
+    for i in range(count):
+        N = int(rng.choice([64, 96, 128, 192, 256]))
+        era = int(rng.choice([ah.AH_RADIATION, ah.AH_MATTER]))
+        s = float(rng.choice([0.0, 1.0]))
+        cfgs.append(ah.config(N, era=era, s=s, seed=100 + i, precision=ah.AH_FP32))
+    return cfgs
+
+
+def run_batch(ah, torch):
+    cfgs = batch_configs(ah)
+    series, st = ah.ah_batch_run(cfgs, flags=ah.AH_BATCH_AUTOTUNE, series_cap=2)
+    rate = st["site_updates"] / st["seconds"]
+    # looping the single-lattice paths over a sample of the same lattices
+    sample = sorted(range(len(cfgs)), key=lambda i: cfgs[i].N)[::8][:6]
+
+    def loop(kernel):
+        su, t = 0.0, 0.0
+        for i in sample:
+            c = cfgs[i]
+            n = int(round((c.tau_end - c.tau0) / c.dt))
+            g = ah.Sim(c.N, era=c.era, s=c.s, seed=c.seed, kernel=kernel)
+            g.sync()
+            t0 = time.perf_counter()
+            g.step(n)
+            g.observables()
+            t += time.perf_counter() - t0
+            su += c.N ** 3 * n
+            g.close()
+        return su / t
+
+    loop_fused = loop(ah.AH_KERNEL_FUSED)
+    loop_plain = loop(ah.AH_KERNEL_PLAIN)
+    return {"workload": "64 FP32 lattices, N ~ U{64,96,128,192,256}, era and s uniform, seeds 100-163, "
+                        "each to tau = N dx / 2; diagnostics at start and end",
+            "sims_per_hour": st["sims_per_hour"], "site_updates_per_s": rate, "seconds": st["seconds"],
+            "setup_seconds": st["setup_seconds"], "site_updates": st["site_updates"], "shape": st["shape"],
+            "launches": st["launches"], "graph_replays": st["rounds"],
+            "loop_fused_site_updates_per_s": loop_fused, "loop_plain_fp32_site_updates_per_s": loop_plain,
+            "speedup_vs_loop_plain": rate / loop_plain, "speedup_vs_loop_fused": rate / loop_fused,
+            "loop_sample": "%d of the lattices (N = %s), each alone to its end" % (
+                len(sample), ",".join(str(cfgs[i].N) for i in sample))}
+
+
+def run_serve(ah, nreq, rate=2.0, seed=5, budget=150 << 30):
+    """Poisson arrivals (mean `rate`/s) of runs with N in {64,128,192,256,384}
+    (weights .3/.3/.2/.15/.05), era and s uniform, fresh seeds, each to
+    tau = N dx / 2, diagnostics every 20 steps, 150 GB budget."""
+    import numpy as np
+    rng = np.random.Generator(np.random.PCG64(seed))
+    Ns = rng.choice([64, 128, 192, 256, 384], size=nreq, p=[0.3, 0.3, 0.2, 0.15, 0.05])
+    gaps = rng.exponential(1.0 / rate, size=nreq)
+    cfgs = [ah.config(int(N), era=int(rng.choice([ah.AH_RADIATION, ah.AH_MATTER])),
+                      s=float(rng.choice([0.0, 1.0])), seed=1000 + i, diag_every=20, precision=ah.AH_FP32)
+            for i, N in enumerate(Ns)]
+    ids = []
+    with ah.Server(budget, max_slots=64) as srv:
+        t0 = time.perf_counter()
+        t_next = 0.0
+        for c, gap in zip(cfgs, gaps):
+            t_next += gap
+            d = t_next - (time.perf_counter() - t0)
+            if d > 0:
+                time.sleep(d)
+            ids.append(srv.submit(c))
+        res = []
+        for rid in ids:
+            while True:
+                r = srv.poll(rid)
+                if r is not None:
+                    res.append(r)
+                    break
+                time.sleep(0.002)
+        st = srv.stats()
+    lat = np.array([td - ts for _, ts, td in res])
+    first = min(ts for _, ts, _ in res)
+    last = max(td for _, _, td in res)
+    su = sum(c.N ** 3 * int(round((c.tau_end - c.tau0) / c.dt)) for c in cfgs)
+    return {"workload": "Poisson arrivals, mean 2/s, N in {64,128,192,256,384} (weights .3/.3/.2/.15/.05), "
+                        "era and s uniform, each to tau = N dx / 2, diagnostics every 20 steps, 150 GB budget",
+            "requests": nreq, "sims_per_hour": nreq * 3600.0 / (last - first),
+            "p50_latency_s": float(np.percentile(lat, 50)), "p99_latency_s": float(np.percentile(lat, 99)),
+            "mean_latency_s": float(lat.mean()), "site_updates_per_s": su / (last - first),
+            "offered_site_updates_per_s": su / float(np.sum(gaps)), "launches": st["launches"],
+            "sample": "%d requests (the full workload is 500)" % nreq if nreq < 500 else "full 500 requests"}
+
+
 def reference_arm(a, wl, rank, world):
     """The CPU oracle as it stands, timed on the host cores; rank 0 only."""
     if rank != 0:
@@ -222,7 +320,8 @@ def main():
     N, prec, era, s, seed, diag_every, desc = WORKLOADS[wl]
     n_sites = N ** 3
     stream = torch.cuda.Stream()
-    g = ah.Sim(N, precision=prec, kernel=ah.AH_KERNEL_FUSED, era=era, s=s, seed=seed + 1000 * rank)
+    g = ah.Sim(N, precision=prec, kernel=ah.AH_KERNEL_FUSED, era=era, s=s, seed=seed + 1000 * rank,
+               flags=ah.AH_FLAG_AUTOTUNE)
     ah.ah_set_stream(g.h, stream.cuda_stream)
     info = g.info
 
@@ -283,7 +382,8 @@ def main():
     achieved = alg_bytes / avg_launch_s / 1e9
     tr = traffic_per_launch(n_sites)
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": tr, "kernel": "k_fused (one leapfrog step)", "peak_source": peak_src,
+                "traffic": tr if info["variant_name"] == TRAFFIC_VARIANT else None,
+                "kernel": "fused step, shape %s (one leapfrog step)" % info["variant_name"], "peak_source": peak_src,
                 "alg_bytes_per_launch": alg_bytes, "avg_launch_ms": avg_launch_s * 1e3,
                 "step_share_of_time": step_ms / t_ms}
 
@@ -310,6 +410,12 @@ def main():
         except ah.AhError as e:
             plain = {"unavailable": str(e)}
 
+    batch = serve = None
+    if rank == 0 and not a.no_batch:
+        batch = run_batch(ah, torch)
+    if rank == 0 and not a.no_serve:
+        serve = run_serve(ah, a.serve_requests)
+
     cpu = None
     if rank == 0 and world == 1 and not a.no_cpu:
         rate, cores, sample = cpu_oracle_rate(wl)
@@ -330,7 +436,9 @@ def main():
             "plain_fp64": plain,
             "e2e": {"value": e2e_value, "unit": "site-updates/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": d2h},
-            "gpu_launches": a.steps * (diag_every * info["step_launches"] + 2),
+            "gpu_launches": a.steps * (diag_every * info["step_launches"] + 3),
+            "batch": batch,
+            "serve": serve,
             "clocks": clocks,
             "final_obs": {k: final_obs[k] for k in ("step", "tau", "xi_L", "xi_W", "v2_V", "v2_L", "v2_omega",
                                                      "gauss_rel", "max_abs_theta")},

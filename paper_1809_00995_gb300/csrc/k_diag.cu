@@ -20,7 +20,9 @@
 // + c(z1 z2 z3*, z4*) along the chain that forms the plaquette product.  This is
 // exactly the arctangent formula whenever none of z1, z2, z3*, z4* and the
 // product lies within a relative margin of the negative real axis (where the
-// branch of Arg is decided by rounding); such plaquettes are appended to a list
+// branch of Arg is decided by rounding).  Each edge product is first scaled to
+// unit size (Arg unchanged), so the chain cannot underflow where |phi| is
+// small.  The plaquettes left undecided are appended to a list
 // and evaluated by k_diag_fixup with the FP64 arctangent formula, so the counts
 // are those of the FP64 formula on the same snapshot.
 //
@@ -64,14 +66,22 @@ __device__ __forceinline__ double arg_pi(C2<double> z)
 // of ten between the two.  For FP64 data only values exactly on the axis (or
 // zero) are sent there.
 template <typename T> struct Margin;
-template <> struct Margin<float> { static constexpr float v = 1.0f / 32768.0f; static constexpr float tiny = 1e-30f; };
+template <> struct Margin<float> { static constexpr float v = 1.0f / 32768.0f; static constexpr float tiny = 1e-36f; };
 template <> struct Margin<double> { static constexpr double v = 0.0; static constexpr double tiny = 1e-300; };
 
 template <typename T>
 __device__ __forceinline__ bool near_cut(C2<T> z)
 {
-    const T ar = fabs(z.r), ai = fabs(z.i);
-    return (z.r < T(0) && ai <= Margin<T>::v * ar) || (ar + ai < Margin<T>::tiny);
+    return z.r < T(0) && fabs(z.i) <= Margin<T>::v * fabs(z.r);
+}
+// z divided by max(|Re z|, |Im z|): same Arg, magnitude in [1, sqrt 2], so the
+// chained products cannot underflow when |phi| is small; *m receives the divisor.
+template <typename T>
+__device__ __forceinline__ C2<T> unit_scale(C2<T> z, T *m)
+{
+    *m = fmax(fabs(z.r), fabs(z.i));
+    const T s = *m > Margin<T>::tiny ? T(1) / *m : T(1);
+    return { z.r * s, z.i * s };
 }
 // carry c of Arg u + Arg v = Arg(uv) + 2 pi c, Arg in (-pi, pi]
 template <typename T>
@@ -87,6 +97,12 @@ __device__ __forceinline__ int carry(C2<T> u, C2<T> v, C2<T> uv)
 template <typename T>
 __device__ __forceinline__ int winding_carry(C2<T> z1, C2<T> z2, C2<T> z3, C2<T> z4)
 {
+    T m1, m2, m3, m4;
+    z1 = unit_scale(z1, &m1);
+    z2 = unit_scale(z2, &m2);
+    z3 = unit_scale(z3, &m3);
+    z4 = unit_scale(z4, &m4);
+    if (!(fmin(fmin(m1, m2), fmin(m3, m4)) > Margin<T>::tiny)) return INT_MIN;   // (near) zero edge product
     const C2<T> w3 = conj(z3), w4 = conj(z4);
     const C2<T> q2 = cmul(z1, z2), q3 = cmul(q2, w3), q4 = cmul(q3, w4);
     if (near_cut(z1) | near_cut(z2) | near_cut(w3) | near_cut(w4) | near_cut(q4)) return INT_MIN;

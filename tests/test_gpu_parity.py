@@ -233,12 +233,12 @@ def test_exact_diagnostics_flag_matches_oracle(precision):
 
 
 @pytest.mark.parametrize("precision", [ah.AH_FP64, ah.AH_FP32])
-@pytest.mark.parametrize("kind", ["random", "large_theta", "real_fields", "strings"])
+@pytest.mark.parametrize("kind", ["random", "large_theta", "real_fields", "strings", "tiny_phi"])
 def test_windings_bit_exact_on_hard_snapshots(precision, kind):
     """Windings of the fast path equal the FP64 arctangent formula on snapshots
     with many plaquettes at or near a branch cut: random fields, link phases far
     outside (-pi, pi], real fields with zero links (edge products exactly on the
-    real axis), and analytic strings."""
+    real axis), analytic strings, and fields of magnitude 1e-5."""
     N = 16
     if kind == "random":
         f = random_state(N, 31, phi_amp=1.0, th_amp=3.0)
@@ -248,8 +248,11 @@ def test_windings_bit_exact_on_hard_snapshots(precision, kind):
         f = random_state(N, 33)
         f[1] = 0.0
         f[4:7] = 0.0
-    else:
+    elif kind == "strings":
         f = straight_strings(N, axis=1, x0=0.5, y0=0.25)
+    else:                           # |phi| ~ 1e-5: products of four edge values would underflow FP32
+        f = random_state(N, 34, th_amp=2.0)
+        f[0:2] *= 1e-5
     with sim(N, precision, ah.AH_KERNEL_FUSED) as g:
         g.set_fields(f)
         snap = g.fields()

@@ -60,6 +60,8 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-ensemble measurement")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving measurement")
+    ap.add_argument("--variant", default=None,
+                    help="fused-step shape by name (default: autotuned), e.g. ty8_b4")
     ap.add_argument("--serve-requests", type=int, default=40,
                     help="requests of the serving run (500 for the full workload; 2 per second)")
     return ap.parse_args()
@@ -321,7 +323,16 @@ def main():
     n_sites = N ** 3
     stream = torch.cuda.Stream()
     g = ah.Sim(N, precision=prec, kernel=ah.AH_KERNEL_FUSED, era=era, s=s, seed=seed + 1000 * rank,
-               flags=ah.AH_FLAG_AUTOTUNE)
+               flags=0 if a.variant else ah.AH_FLAG_AUTOTUNE)
+    if a.variant:
+        names = {}
+        for v in range(ah.ah_variant_count(prec)):
+            try:
+                g.set_variant(v)
+                names[g.info["variant_name"]] = v
+            except ah.AhError:
+                pass
+        g.set_variant(names[a.variant])
     ah.ah_set_stream(g.h, stream.cuda_stream)
     info = g.info
 

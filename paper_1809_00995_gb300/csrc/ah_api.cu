@@ -281,8 +281,12 @@ ah_status do_diag(ah_sim *h, Box b, ah_obs *out)
     const DiagCoef dc = diag_coef(h->cfg, h->step);
     const View<real> v = make_view(F, h->cur, false);
     const bool exact = (h->cfg.flags & AH_FLAG_EXACT_DIAG) != 0;
-    AH_CUDA(launch_diag<real>(v, h->N, b, dc, h->partials, h->diag_blocks, h->result, h->list, exact,
-                              h->stream));
+    const bool whole = b.x0 == 0 && b.y0 == 0 && b.z0 == 0 && b.nx == h->N && b.ny == h->N && b.nz == h->N;
+    if (whole && !exact)
+        AH_CUDA(launch_diag_whole<real>(v, h->N, dc, h->partials, h->result, h->list, h->diag_blocks, h->stream));
+    else
+        AH_CUDA(launch_diag<real>(v, h->N, b, dc, h->partials, h->diag_blocks, h->result, h->list, exact,
+                                  h->stream));
     AH_CUDA(cudaMemcpyAsync(h->host_result, h->result, sizeof(DiagPartial), cudaMemcpyDeviceToHost,
                             h->stream));
     AH_CUDA(cudaMemcpyAsync(h->host_count, h->list.count, sizeof(unsigned long long),
@@ -442,10 +446,11 @@ ah_status ah_create_ex(const ah_config *cfg, ah_sim **out)
     const size_t esz = cfg->precision == AH_FP32 ? sizeof(float) : sizeof(double);
     h->dbytes = 15 * padded((size_t)h->nsites) * esz;
     h->diag_blocks = diag_grid_blocks(h->num_sms);
+    const int nparts = std::max(h->diag_blocks, fused_diag_ctas(h->N));
     // expected near-cut plaquettes: about 5e-5 of the 3 N^3 plaquettes in FP32
     h->list.capacity = std::max<long long>(1LL << 20, h->nsites * 3 / 2000);
     e = cudaMalloc(&h->dmem, h->dbytes);
-    if (e == cudaSuccess) e = cudaMalloc((void **)&h->partials, sizeof(DiagPartial) * (h->diag_blocks + 1));
+    if (e == cudaSuccess) e = cudaMalloc((void **)&h->partials, sizeof(DiagPartial) * (nparts + 1));
     if (e == cudaSuccess)
         e = cudaMalloc((void **)&h->list.count, sizeof(unsigned long long) * (1 + h->list.capacity));
     if (e == cudaSuccess) e = cudaMallocHost((void **)&h->host_result, sizeof(DiagPartial) + 32);
@@ -453,7 +458,7 @@ ah_status ah_create_ex(const ah_config *cfg, ah_sim **out)
         ah_destroy(h);
         return fail(AH_ERR_OOM, "allocation of %.3g GB failed: %s", h->dbytes / 1e9, cudaGetErrorString(e));
     }
-    h->result = h->partials + h->diag_blocks;
+    h->result = h->partials + nparts;
     h->list.items = h->list.count + 1;
     h->host_count = (unsigned long long *)(h->host_result + 1);
     h->host_err = (int *)(h->host_count + 1);

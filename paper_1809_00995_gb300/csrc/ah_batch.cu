@@ -294,6 +294,7 @@ ah_status check_batch_cfg(const ah_config &c)
 {
     if (c.precision != AH_FP32) return host_fail(AH_ERR_ARG, "batched lattices must be FP32 (precision AH_FP32)");
     if (c.diag_every < 0) return host_fail(AH_ERR_ARG, "diag_every must be >= 0");
+    if (c.N > 1290) return host_fail(AH_ERR_ARG, "batched lattices need N <= 1290 (32-bit site indices)");
     return host_validate(c);
 }
 

@@ -63,6 +63,7 @@ struct DiagPartial {
 };
 
 struct Box { int x0, y0, z0, nx, ny, nz; };
+struct DiagList;
 
 // Plaquettes whose winding the fast diagnostics leave to the FP64 path:
 // items[k] = site index * 4 + orientation (0: 12, 1: 13, 2: 23).
@@ -106,6 +107,26 @@ cudaError_t launch_diag(const View<real> &v, int N, Box b, const DiagCoef &c,
                         DiagList list, bool exact, cudaStream_t st);
 
 int diag_grid_blocks(int num_sms);
+
+// Whole-lattice diagnostics through the fused step's tile walk (tile 32 x 8,
+// nothing written back): one DiagPartial per CTA of the grid that
+// fused_diag_grid gives (fused_diag_ctas of them), near-cut plaquettes
+// appended to the list.
+struct DiagArgs {
+    DiagCoef dc;
+    DiagPartial *partials;
+    DiagList list;
+};
+void fused_diag_grid(int N, int *tx, int *ty, int *nch, int *zc);
+int fused_diag_ctas(int N);
+template <typename real>
+cudaError_t launch_fused_diag(const View<real> &v, int N, const DiagArgs &da, cudaStream_t st);
+// The whole fast diagnostic: clear the list, launch_fused_diag, sum the
+// partials in a fixed order into *result, FP64 windings of the listed
+// plaquettes (fix_blocks x 128 threads).
+template <typename real>
+cudaError_t launch_diag_whole(const View<real> &v, int N, const DiagCoef &c, DiagPartial *partials,
+                              DiagPartial *result, DiagList list, int fix_blocks, cudaStream_t st);
 
 // Host helpers of ah_api.cu shared with other translation units.
 KickCoef<float> host_kick_coef32(const ah_config &c, int64_t step);

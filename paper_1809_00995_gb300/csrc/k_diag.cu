@@ -37,6 +37,7 @@
 #include <mutex>
 
 #include "ah_internal.cuh"
+#include "diag_common.cuh"
 #include "sincos32.cuh"
 
 namespace ah {
@@ -45,68 +46,12 @@ namespace {
 constexpr int TX = 32, TY = 8, NT = TX * TY;
 constexpr double kPi = 3.141592653589793;
 
-template <typename T>
-struct C2 { T r, i; };
-template <typename T>
-__device__ __forceinline__ C2<T> cmul(C2<T> a, C2<T> b) { return { a.r * b.r - a.i * b.i, a.r * b.i + a.i * b.r }; }
-template <typename T>
-__device__ __forceinline__ C2<T> conj(C2<T> a) { return { a.r, -a.i }; }
 __device__ __forceinline__ C2<double> expi(double t) { double s, c; sincos(t, &s, &c); return { c, s }; }
 __device__ __forceinline__ C2<float> expi(float t) { float s, c; sincos_link(t, &s, &c); return { c, s }; }
 __device__ __forceinline__ double arg_pi(C2<double> z)
 {
     const double a = atan2(z.i, z.r);
     return a == -kPi ? kPi : a;
-}
-
-// Relative margin to the negative real axis below which a winding is decided
-// by the FP64 path instead of the FP32 carries.  An FP32 edge product
-// conj(phi^a) U phi^b (U from sincos_link, error < 1e-7) has a relative error below
-// 1e-6, the product of four of them below 3e-6; 2^-15 (3.1e-5) keeps a factor
-// of ten between the two.  For FP64 data only values exactly on the axis (or
-// zero) are sent there.
-template <typename T> struct Margin;
-template <> struct Margin<float> { static constexpr float v = 1.0f / 32768.0f; static constexpr float tiny = 1e-36f; };
-template <> struct Margin<double> { static constexpr double v = 0.0; static constexpr double tiny = 1e-300; };
-
-template <typename T>
-__device__ __forceinline__ bool near_cut(C2<T> z)
-{
-    return z.r < T(0) && fabs(z.i) <= Margin<T>::v * fabs(z.r);
-}
-// z divided by max(|Re z|, |Im z|): same Arg, magnitude in [1, sqrt 2], so the
-// chained products cannot underflow when |phi| is small; *m receives the divisor.
-template <typename T>
-__device__ __forceinline__ C2<T> unit_scale(C2<T> z, T *m)
-{
-    *m = fmax(fabs(z.r), fabs(z.i));
-    const T s = *m > Margin<T>::tiny ? T(1) / *m : T(1);
-    return { z.r * s, z.i * s };
-}
-// carry c of Arg u + Arg v = Arg(uv) + 2 pi c, Arg in (-pi, pi]
-template <typename T>
-__device__ __forceinline__ int carry(C2<T> u, C2<T> v, C2<T> uv)
-{
-    const bool su = u.i >= T(0), sv = v.i >= T(0);
-    if (su && sv) return uv.i < T(0) ? 1 : 0;
-    if (!su && !sv) return uv.i >= T(0) ? -1 : 0;
-    return 0;
-}
-// Winding of a plaquette from its four edge products (orientation as Eq. 9),
-// or INT_MIN when it must be decided by the FP64 path.
-template <typename T>
-__device__ __forceinline__ int winding_carry(C2<T> z1, C2<T> z2, C2<T> z3, C2<T> z4)
-{
-    T m1, m2, m3, m4;
-    z1 = unit_scale(z1, &m1);
-    z2 = unit_scale(z2, &m2);
-    z3 = unit_scale(z3, &m3);
-    z4 = unit_scale(z4, &m4);
-    if (!(fmin(fmin(m1, m2), fmin(m3, m4)) > Margin<T>::tiny)) return INT_MIN;   // (near) zero edge product
-    const C2<T> w3 = conj(z3), w4 = conj(z4);
-    const C2<T> q2 = cmul(z1, z2), q3 = cmul(q2, w3), q4 = cmul(q3, w4);
-    if (near_cut(z1) | near_cut(z2) | near_cut(w3) | near_cut(w4) | near_cut(q4)) return INT_MIN;
-    return carry(z1, z2, q2) + carry(q2, w3, q3) + carry(q3, w4, q4);
 }
 
 // FP64 arctangent formula for the plaquette (ii, jj) based at site (x, y, z).
@@ -160,67 +105,12 @@ __device__ long long winding_fp64(const View<real> &v, int N, int ii, int jj, in
     return llrint(tot / (2.0 * kPi));
 }
 
-// Compensated accumulator in the state precision (plain sum for FP64 data).
-template <typename T>
-struct Acc {
-    T s = 0, c = 0;
-    __device__ __forceinline__ void add(T v)
-    {
-        const T y = v - c;
-        const T t = s + y;
-        c = (t - s) - y;
-        s = t;
-    }
-    __device__ __forceinline__ double value() const { return (double)s - (double)c; }
-};
-template <>
-struct Acc<double> {
-    double s = 0;
-    __device__ __forceinline__ void add(double v) { s += v; }
-    __device__ __forceinline__ double value() const { return s; }
-};
-
 __device__ __forceinline__ long long wrap_id(int x, int y, int z, int N)
 {
     x = x >= N ? x - N : (x < 0 ? x + N : x);
     y = y >= N ? y - N : (y < 0 ? y + N : y);
     z = z >= N ? z - N : (z < 0 ? z + N : z);
     return x + (long long)N * (y + (long long)N * z);
-}
-
-// Block-wide reduction into *out (thread 0 writes).
-__device__ void block_reduce(double acc[kNumSums], double mx[kNumMax], long long ic[kNumInt],
-                             DiagPartial *out)
-{
-    __shared__ DiagPartial red[NT / 32];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-#pragma unroll
-        for (int k = 0; k < kNumSums; ++k) acc[k] += __shfl_down_sync(0xffffffffu, acc[k], o);
-#pragma unroll
-        for (int k = 0; k < kNumMax; ++k) mx[k] = fmax(mx[k], __shfl_down_sync(0xffffffffu, mx[k], o));
-#pragma unroll
-        for (int k = 0; k < kNumInt; ++k) ic[k] += __shfl_down_sync(0xffffffffu, ic[k], o);
-    }
-    if (lane == 0) {
-#pragma unroll
-        for (int k = 0; k < kNumSums; ++k) red[warp].sums[k] = acc[k];
-#pragma unroll
-        for (int k = 0; k < kNumMax; ++k) red[warp].maxv[k] = mx[k];
-#pragma unroll
-        for (int k = 0; k < kNumInt; ++k) red[warp].ints[k] = ic[k];
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        DiagPartial r = red[0];
-        for (int w = 1; w < NT / 32; ++w) {
-            for (int k = 0; k < kNumSums; ++k) r.sums[k] += red[w].sums[k];
-            for (int k = 0; k < kNumMax; ++k) r.maxv[k] = fmax(r.maxv[k], red[w].maxv[k]);
-            for (int k = 0; k < kNumInt; ++k) r.ints[k] += red[w].ints[k];
-        }
-        *out = r;
-    }
 }
 
 struct TileIter {
@@ -345,7 +235,7 @@ __global__ void __launch_bounds__(NT) k_diag_fast(View<real> v, int N, Box b, Di
     accd[14] = g2sum;
     accd[15] = gs2sum;
     double mx[kNumMax] = { gmax, (double)tmax };
-    block_reduce(accd, mx, ic, &partials[blockIdx.x]);
+    block_reduce<NT>(accd, mx, ic, &partials[blockIdx.x]);
 }
 
 // FP64 arctangent windings of the listed plaquettes, added to the result.
@@ -447,7 +337,7 @@ __global__ void __launch_bounds__(NT) k_diag_exact(View<real> v, int N, Box b, D
         mx[1] = fmax(mx[1], tmx);
         ic[7] += !(isfinite(L) && isfinite(rho) && isfinite(p) && isfinite(G));
     }
-    block_reduce(acc, mx, ic, &partials[blockIdx.x]);
+    block_reduce<NT>(acc, mx, ic, &partials[blockIdx.x]);
 }
 
 // Sum the partials in index order (one block; thread k owns one output).
@@ -469,9 +359,69 @@ __global__ void k_diag_finish(const DiagPartial *partials, int n, DiagPartial *r
     }
 }
 
+// Sum many partials in a fixed order: lane k of warp c reduces word k of
+// partials [c n/32, (c+1) n/32), then thread k adds the 32 chunk results.
+__global__ void __launch_bounds__(1024) k_diag_sum(const DiagPartial *partials, int n, DiagPartial *result)
+{
+    constexpr int NW = kNumSums + kNumMax + kNumInt;
+    __shared__ double sd[32][kNumSums + kNumMax];
+    __shared__ long long si[32][kNumInt];
+    const int k = threadIdx.x & 31, c = threadIdx.x >> 5;
+    const int per = (n + 31) / 32, b0 = min(n, c * per), b1 = min(n, b0 + per);
+    if (k < kNumSums) {
+        double s = 0.0;
+        for (int b = b0; b < b1; ++b) s += partials[b].sums[k];
+        sd[c][k] = s;
+    } else if (k < kNumSums + kNumMax) {
+        double m = 0.0;
+        for (int b = b0; b < b1; ++b) m = fmax(m, partials[b].maxv[k - kNumSums]);
+        sd[c][k] = m;
+    } else if (k < NW) {
+        long long s = 0;
+        for (int b = b0; b < b1; ++b) s += partials[b].ints[k - kNumSums - kNumMax];
+        si[c][k - kNumSums - kNumMax] = s;
+    }
+    __syncthreads();
+    const int t = threadIdx.x;
+    if (t < kNumSums) {
+        double s = 0.0;
+        for (int q = 0; q < 32; ++q) s += sd[q][t];
+        result->sums[t] = s;
+    } else if (t < kNumSums + kNumMax) {
+        double m = 0.0;
+        for (int q = 0; q < 32; ++q) m = fmax(m, sd[q][t]);
+        result->maxv[t - kNumSums] = m;
+    } else if (t < NW) {
+        long long s = 0;
+        for (int q = 0; q < 32; ++q) s += si[q][t - kNumSums - kNumMax];
+        result->ints[t - kNumSums - kNumMax] = s;
+    }
+}
+
 }  // namespace
 
 int diag_grid_blocks(int num_sms) { return num_sms * 4; }
+
+template <typename real>
+cudaError_t launch_diag_whole(const View<real> &v, int N, const DiagCoef &c, DiagPartial *partials,
+                              DiagPartial *result, DiagList list, int fix_blocks, cudaStream_t st)
+{
+    cudaError_t e = cudaMemsetAsync(list.count, 0, sizeof(unsigned long long), st);
+    if (e != cudaSuccess) return e;
+    DiagArgs da;
+    da.dc = c;
+    da.partials = partials;
+    da.list = list;
+    e = launch_fused_diag<real>(v, N, da, st);
+    if (e != cudaSuccess) return e;
+    k_diag_sum<<<1, 1024, 0, st>>>(partials, fused_diag_ctas(N), result);
+    k_diag_fixup<real><<<fix_blocks, 128, 0, st>>>(v, N, list, result);
+    return cudaGetLastError();
+}
+template cudaError_t launch_diag_whole<float>(const View<float> &, int, const DiagCoef &, DiagPartial *,
+                                              DiagPartial *, DiagList, int, cudaStream_t);
+template cudaError_t launch_diag_whole<double>(const View<double> &, int, const DiagCoef &, DiagPartial *,
+                                               DiagPartial *, DiagList, int, cudaStream_t);
 
 template <typename real>
 cudaError_t launch_diag(const View<real> &v, int N, Box b, const DiagCoef &c, DiagPartial *partials,

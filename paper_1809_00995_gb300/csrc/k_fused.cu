@@ -19,10 +19,15 @@
 // state exactly once from DRAM; halo re-reads are served by L2.  Periodic
 // boundaries are applied in the index arithmetic.
 #include "ah_internal.cuh"
+#include "diag_common.cuh"
 #include "sincos32.cuh"
 
 namespace ah {
 namespace {
+
+// Kernel modes: the step, or the diagnostics of the current state (the same
+// tile walk with nothing written back).
+enum { MODE_STEP = 0, MODE_DIAG = 1 };
 
 template <typename real>
 struct cpx { real r, i; };
@@ -38,6 +43,19 @@ __device__ __forceinline__ real plaq(cpx<real> a, cpx<real> b, cpx<real> c, cpx<
 {
     const cpx<real> ab = mul(a, b), cd = mul(c, d);
     return ab.i * cd.r - ab.r * cd.i;
+}
+// (a b) conj(c d) = e^{i Xi}: sine in .i, cosine in .r
+template <typename real>
+__device__ __forceinline__ cpx<real> plaq2(cpx<real> a, cpx<real> b, cpx<real> c, cpx<real> d)
+{
+    const cpx<real> ab = mul(a, b), cd = mul(c, d);
+    return { ab.r * cd.r + ab.i * cd.i, ab.i * cd.r - ab.r * cd.i };
+}
+// 1 - cos Xi from e^{i Xi} = (c, s) without cancellation
+template <typename real>
+__device__ __forceinline__ real one_minus_cos(cpx<real> e)
+{
+    return e.r > real(0) ? e.i * e.i / (real(1) + e.r) : real(1) - e.r;
 }
 
 __device__ __forceinline__ int wrapm(int a, int N)
@@ -79,9 +97,14 @@ template <> struct Row<double, 2> {
 
 // Each thread owns RX consecutive sites in x times RY rows (y stride 8).
 // One work item of the fused step: tile (bx, by) of plane chunk bz, marched in z.
-template <typename real, int TY, int RX>
+template <int V> struct IC { static constexpr int value = V; };
+
+// IT: site-index type (int when N^3 < 2^31, so every field address is one
+// 32 x 32 -> 64-bit multiply-add; long long otherwise).
+template <typename real, int TY, int RX, typename IT, int MODE = MODE_STEP>
 __device__ __forceinline__ void fused_tile(const View<real> &v, int N, int zc, const KickCoef<real> &c,
-                                           int bx, int by, int bz, unsigned char *smem_raw)
+                                           int bx, int by, int bz, unsigned char *smem_raw,
+                                           const DiagArgs *da = nullptr)
 {
     using G = Geo<real, TY, RX>;
     using IO = Row<real, RX>;
@@ -93,9 +116,49 @@ __device__ __forceinline__ void fused_tile(const View<real> &v, int N, int zc, c
     const int tid = threadIdx.x, lx = tid & 31, wy = tid >> 5;
     const int x0 = bx * TX, y0 = by * TY;
     const int z0 = bz * zc;
-    if (z0 >= N) return;
+    constexpr bool STEP = MODE == MODE_STEP, DIAG = MODE == MODE_DIAG;
+    // per-thread diagnostic accumulators (MODE_DIAG): the energy sums of
+    // ah_obs (compensated, state precision), the Gauss residual sums and max
+    // (FP64), max |theta|, winding counters, non-finite sites
+    Acc<real> dacc[14];
+    real dtmax = real(0);
+    long long dic[kNumInt] = { 0, 0, 0, 0, 0, 0, 0, 0 };
+    // Gauss residual G = g_div div E + g_phi Im(conj(phi) Pi): FP64 for FP64
+    // data; for FP32 data in double-float arithmetic (each G to about 2^-44 of
+    // |g_div div E| + |g_phi Im(conj(phi) Pi)|), G^2 and that scale^2 summed
+    // with compensation after scaling by 2^60, max |G| kept as a double-float
+    double dg2 = 0.0, dgs2 = 0.0, dgmax = 0.0;
+    Acc<float> fg2, fgs2;
+    DF fgmax{ 0.f, 0.f };
+    DF cg_div{ 0.f, 0.f }, cg_phi{ 0.f, 0.f };
+    real k_inv_dx2 = 0, k_v = 0, k_eel = 0, k_b = 0, k_sig2 = 0;
+    if constexpr (DIAG) {
+        const DiagCoef &dc = da->dc;
+        cg_div = df_from(dc.g_div);
+        cg_phi = df_from(dc.g_phi);
+        k_inv_dx2 = (real)dc.inv_dx2; k_v = (real)dc.v_coef; k_eel = (real)dc.eel_coef;
+        k_b = (real)dc.b_coef; k_sig2 = (real)dc.sigma2;
+    }
+    auto diag_flush = [&]() {
+        if constexpr (DIAG) {
+            double accd[kNumSums];
+#pragma unroll
+            for (int k = 0; k < 14; ++k) accd[k] = dacc[k].value();
+            if constexpr (sizeof(real) == 4) {
+                dg2 = fg2.value() * 0x1p-60;
+                dgs2 = fgs2.value() * 0x1p-60;
+                dgmax = (double)fgmax.h + (double)fgmax.l;
+            }
+            accd[14] = dg2;
+            accd[15] = dgs2;
+            double mx[kNumMax] = { dgmax, (double)dtmax };
+            const int cta = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
+            block_reduce<256>(accd, mx, dic, &da->partials[cta]);
+        }
+    };
+    if (z0 >= N) { diag_flush(); return; }
     const int z1 = min(z0 + zc, N);
-    const long long NN = (long long)N * N;
+    const IT NN = (IT)N * (IT)N;
 
     // own rows: in-plane offset of the first of the RX sites, validity
     int roff[RY];
@@ -124,11 +187,12 @@ __device__ __forceinline__ void fused_tile(const View<real> &v, int N, int zc, c
 
     // register prefetch of one plane's phi, theta: own sites [0, NS), halo [NS]
     real fth[NS + 1][3], fph[NS + 1][2];
-    auto load_plane = [&](int z) {
-        const long long base = (long long)wrapm(z, N) * NN;
+    auto load_plane = [&](int z) {           // z in [-1, N + 1]
+        const int zz = z < 0 ? z + N : (z >= N ? z - N : z);
+        const IT base = (IT)zz * NN;
 #pragma unroll
         for (int my = 0; my < RY; ++my) {
-            const long long s = base + roff[my];
+            const IT s = base + (IT)roff[my];
             real t[RX];
             IO::ld(v.th1 + s, t);
 #pragma unroll
@@ -147,7 +211,7 @@ __device__ __forceinline__ void fused_tile(const View<real> &v, int N, int zc, c
             for (int mx = 0; mx < RX; ++mx) fph[my * RX + mx][1] = t[mx];
         }
         if (has_halo) {
-            const long long s = base + hoff;
+            const IT s = base + (IT)hoff;
             fth[NS][0] = v.th1[s]; fth[NS][1] = v.th2[s]; fth[NS][2] = v.th3[s];
             fph[NS][0] = v.phr[s]; fph[NS][1] = v.phi[s];
         }
@@ -172,10 +236,17 @@ __device__ __forceinline__ void fused_tile(const View<real> &v, int N, int zc, c
     // own-site registers carried along z
     cpx<real> ph_m[NS], ph_0[NS], u3_m[NS];
     real th_0[NS][3], p13_m[NS], p23_m[NS];
+    real e3_m[NS];                           // MODE_DIAG: E_3 of plane z-1
+    if constexpr (DIAG) {
+        const IT base = (IT)(z0 == 0 ? N - 1 : z0 - 1) * NN;
+#pragma unroll
+        for (int m = 0; m < NS; ++m) e3_m[m] = v.e3[base + (IT)roff[m / RX] + (IT)(m % RX)];
+    }
 
     // prologue: planes z0-1 and z0
+    // ring slot of plane z: (z - z0 + 1) & 1
     load_plane(z0 - 1);
-    const int bm = (z0 - 1) & 1, b0 = z0 & 1;
+    constexpr int bm = 0, b0 = 1;
     store_plane(bm);
 #pragma unroll
     for (int m = 0; m < NS; ++m) ph_m[m] = { fph[m][0], fph[m][1] };
@@ -198,14 +269,15 @@ __device__ __forceinline__ void fused_tile(const View<real> &v, int N, int zc, c
     }
     __syncthreads();
 
-    for (int z = z0; z < z1; ++z) {
-        const int bc = z & 1, bn = (z + 1) & 1;
-        const long long base = (long long)z * NN;
+    // one plane z; BC (compile time) is the ring slot of plane z
+    auto plane_step = [&](int z, auto bc_tag) {
+        constexpr int bc = decltype(bc_tag)::value, bn = 1 - bc;
+        const IT base = (IT)z * NN;
         // Pi, E of plane z (consumed after two barriers)
         real pr[NS], pim[NS], e1[NS], e2[NS], e3[NS];
 #pragma unroll
         for (int my = 0; my < RY; ++my) {
-            const long long s = base + roff[my];
+            const IT s = base + (IT)roff[my];
             IO::ld(v.pir + s, pr + my * RX);
             IO::ld(v.pii + s, pim + my * RX);
             IO::ld(v.e1 + s, e1 + my * RX);
@@ -226,13 +298,21 @@ __device__ __forceinline__ void fused_tile(const View<real> &v, int N, int zc, c
 
         // B: plaquette sines of plane z on the tile (own sites) and its low halos
         const cpx<real> *U0 = sU + bc * 3 * NE, *U1p = sU + bn * 3 * NE;
-        real p12[NS], p13[NS], p23[NS];
+        real p12[NS], p13[NS], p23[NS], bcos[NS];
 #pragma unroll
         for (int m = 0; m < NS; ++m) {
             const int e = eix(m), p = pix(m);
-            p12[m] = plaq(U0[e], U0[NE + e + 1], U0[e + EX], U0[NE + e]);
-            p13[m] = plaq(U0[e], U0[2 * NE + e + 1], U1p[e], U0[2 * NE + e]);
-            p23[m] = plaq(U0[NE + e], U0[2 * NE + e + EX], U1p[NE + e], U0[2 * NE + e]);
+            if constexpr (DIAG) {
+                const cpx<real> x12 = plaq2(U0[e], U0[NE + e + 1], U0[e + EX], U0[NE + e]);
+                const cpx<real> x13 = plaq2(U0[e], U0[2 * NE + e + 1], U1p[e], U0[2 * NE + e]);
+                const cpx<real> x23 = plaq2(U0[NE + e], U0[2 * NE + e + EX], U1p[NE + e], U0[2 * NE + e]);
+                p12[m] = x12.i; p13[m] = x13.i; p23[m] = x23.i;
+                bcos[m] = one_minus_cos(x12) + one_minus_cos(x13) + one_minus_cos(x23);
+            } else {
+                p12[m] = plaq(U0[e], U0[NE + e + 1], U0[e + EX], U0[NE + e]);
+                p13[m] = plaq(U0[e], U0[2 * NE + e + 1], U1p[e], U0[2 * NE + e]);
+                p23[m] = plaq(U0[NE + e], U0[2 * NE + e + EX], U1p[NE + e], U0[2 * NE + e]);
+            }
             sP[p] = p12[m];
             sP[G::NP + p] = p13[m];
             sP[2 * G::NP + p] = p23[m];
@@ -277,6 +357,91 @@ __device__ __forceinline__ void fused_tile(const View<real> &v, int N, int zc, c
             const real ne1 = c.c_edamp * e1[m] + c.c_cur * cu1 - c.c_curl * cl1;
             const real ne2 = c.c_edamp * e2[m] + c.c_cur * cu2 - c.c_curl * cl2;
             const real ne3 = c.c_edamp * e3[m] + c.c_cur * cu3 - c.c_curl * cl3;
+            if constexpr (DIAG) if (wr[m / RX]) {
+                const cpx<real> *F1 = sF + bn * NE;
+                const real K = pr[m] * pr[m] + pim[m] * pim[m];
+                const real d1r = w1.r - f0.r, d1i = w1.i - f0.i, d2r = w2.r - f0.r, d2i = w2.i - f0.i;
+                const real d3r = w3.r - f0.r, d3i = w3.i - f0.i;
+                const real G2 = (d1r * d1r + d1i * d1i + d2r * d2r + d2i * d2i + d3r * d3r + d3i * d3i) *
+                                k_inv_dx2;
+                const real m2 = f0.r * f0.r + f0.i * f0.i - k_sig2;
+                const real V = k_v * m2 * m2;
+                const real Eel = k_eel * (e1[m] * e1[m] + e2[m] * e2[m] + e3[m] * e3[m]);
+                const real B = k_b * bcos[m];
+                const real L = K - G2 - V + Eel - B;
+                const real rho = K + G2 + V + Eel + B;
+                const real pp = K - G2 / real(3) - V + (Eel + B) / real(3);
+                dacc[0].add(L); dacc[1].add(rho); dacc[2].add(pp); dacc[3].add(K); dacc[4].add(G2);
+                dacc[5].add(V); dacc[6].add(Eel); dacc[7].add(B); dacc[8].add(K * V); dacc[9].add(G2 * V);
+                dacc[10].add(K * L); dacc[11].add(G2 * L); dacc[12].add(pp * L); dacc[13].add(rho * L);
+                dtmax = fmax(dtmax, fmax(fabs(th_0[m][0]), fmax(fabs(th_0[m][1]), fabs(th_0[m][2]))));
+                dic[7] += !(isfinite(L) && isfinite(rho) && isfinite(pp));
+                const int my = m / RX, mx = m % RX;
+                const int gx = x0 + RX * lx + mx, gy = y0 + wy + 8 * my;
+                // Gauss residual (nothing is written in this mode, so the
+                // backward neighbours' E are the current ones)
+                {
+                    const IT s = base + (IT)roff[my] + (IT)mx;
+                    const real e1b = v.e1[gx == 0 ? s + (IT)(N - 1) : s - 1];
+                    const real e2b = v.e2[gy == 0 ? s + (NN - (IT)N) : s - (IT)N];
+                    if constexpr (sizeof(real) == 8) {
+                        const DiagCoef &dc = da->dc;
+                        const double div = (e1[m] - e1b) + (e2[m] - e2b) + (e3[m] - e3_m[m]);
+                        const double g1 = dc.g_div * div;
+                        const double g2 = dc.g_phi * (f0.r * pim[m] - f0.i * pr[m]);
+                        const double Gs = g1 + g2, gs = fabs(g1) + fabs(g2);
+                        dg2 += Gs * Gs;
+                        dgs2 += gs * gs;
+                        dgmax = fmax(dgmax, fabs(Gs));
+                    } else {
+                        // differences and products of FP32 values are exact as pairs
+                        const DF div = df_add(df_add(two_sum(e1[m], -e1b), two_sum(e2[m], -e2b)),
+                                              two_sum(e3[m], -e3_m[m]));
+                        const DF a = two_prod(f0.r, pim[m]), b = two_prod(f0.i, pr[m]);
+                        const DF g1 = df_mul(cg_div, div), g2 = df_mul(cg_phi, df_add(a, { -b.h, -b.l }));
+                        DF Gs = df_add(g1, g2);
+                        if (Gs.h < 0.f) Gs = { -Gs.h, -Gs.l };
+                        const float gs = fabsf(g1.h) + fabsf(g2.h);
+                        const float sg = Gs.h * 0x1p30f, ss = gs * 0x1p30f;
+                        fg2.add(sg * sg);
+                        fgs2.add(ss * ss);
+                        if (Gs.h > fgmax.h || (Gs.h == fgmax.h && Gs.l > fgmax.l)) fgmax = Gs;
+                    }
+                }
+                // windings of the plaquettes (12), (13), (23) based at x (Eq. 9),
+                // edge products conj(phi^a) (U phi^b) as in k_diag_fast
+                using Z = C2<real>;
+                auto zc_ = [](cpx<real> a) { return Z{ a.r, a.i }; };
+                const Z f0c = conj(zc_(f0));
+                Z z1 = cmul(f0c, zc_(w1)), z2 = cmul(f0c, zc_(w2)), z3 = cmul(f0c, zc_(w3));
+                const Z fx = zc_(F0[e + 1]), fy = zc_(F0[e + EX]), fz = zc_(ph_p[m]);
+                Z z2_1 = cmul(conj(fx), cmul(zc_(U0[NE + e + 1]), zc_(F0[e + 1 + EX])));
+                Z z3_1 = cmul(conj(fx), cmul(zc_(U0[2 * NE + e + 1]), zc_(F1[e + 1])));
+                Z z1_2 = cmul(conj(fy), cmul(zc_(U0[e + EX]), zc_(F0[e + EX + 1])));
+                Z z3_2 = cmul(conj(fy), cmul(zc_(U0[2 * NE + e + EX]), zc_(F1[e + EX])));
+                Z z1_3 = cmul(conj(fz), cmul(zc_(U1p[e]), zc_(F1[e + 1])));
+                Z z2_3 = cmul(conj(fz), cmul(zc_(U1p[NE + e]), zc_(F1[e + EX])));
+                // each of the nine edge products scaled once (three are shared)
+                const bool k1 = unit_scale(z1), k2 = unit_scale(z2), k3 = unit_scale(z3);
+                const bool k21 = unit_scale(z2_1), k31 = unit_scale(z3_1), k12 = unit_scale(z1_2);
+                const bool k32 = unit_scale(z3_2), k13 = unit_scale(z1_3), k23 = unit_scale(z2_3);
+                const int wq[3] = { k1 & k21 & k12 & k2 ? winding_scaled(z1, z2_1, z1_2, z2) : INT_MIN,
+                                    k1 & k31 & k13 & k3 ? winding_scaled(z1, z3_1, z1_3, z3) : INT_MIN,
+                                    k2 & k32 & k23 & k3 ? winding_scaled(z2, z3_2, z2_3, z3) : INT_MIN };
+                const unsigned long long site =
+                    (unsigned long long)((long long)z * N * (long long)N + (long long)roff[my] + mx);
+#pragma unroll
+                for (int q = 0; q < 3; ++q) {
+                    if (wq[q] == INT_MIN) {
+                        const unsigned long long k = atomicAdd(da->list.count, 1ULL);
+                        if (k < (unsigned long long)da->list.capacity) da->list.items[k] = site * 4ULL + q;
+                    } else {
+                        dic[q] += wq[q] < 0 ? -wq[q] : wq[q];
+                        dic[3 + q] += wq[q];
+                        dic[6] += wq[q] != 0;
+                    }
+                }
+            }
             o_pr[m] = npr; o_pi[m] = npi;
             o_e1[m] = ne1; o_e2[m] = ne2; o_e3[m] = ne3;
             o_fr[m] = f0.r + c.dt * npr;
@@ -285,6 +450,7 @@ __device__ __forceinline__ void fused_tile(const View<real> &v, int N, int zc, c
             o_t2[m] = th_0[m][1] + c.dt * ne2;
             o_t3[m] = th_0[m][2] + c.dt * ne3;
             // march: plane z becomes z-1
+            if constexpr (DIAG) e3_m[m] = e3[m];
             ph_m[m] = f0;
             u3_m[m] = u3;
             p13_m[m] = q13;
@@ -294,8 +460,8 @@ __device__ __forceinline__ void fused_tile(const View<real> &v, int N, int zc, c
         }
 #pragma unroll
         for (int my = 0; my < RY; ++my) {
-            if (wr[my]) {
-                const long long s = base + roff[my];
+            if (STEP && wr[my]) {
+                const IT s = base + (IT)roff[my];
                 const int k = my * RX;
                 IO::st(v.pir + s, o_pr + k); IO::st(v.pii + s, o_pi + k);
                 IO::st(v.e1 + s, o_e1 + k); IO::st(v.e2 + s, o_e2 + k); IO::st(v.e3 + s, o_e3 + k);
@@ -304,14 +470,29 @@ __device__ __forceinline__ void fused_tile(const View<real> &v, int N, int zc, c
             }
         }
         __syncthreads();
+    };
+    for (int k = 0; z0 + k < z1; k += 2) {
+        plane_step(z0 + k, IC<1>{});
+        if (z0 + k + 1 < z1) plane_step(z0 + k + 1, IC<0>{});
     }
+    diag_flush();
 }
 
-template <typename real, int TY, int RX, int MINB>
+template <typename real, int TY, int RX, int MINB, typename IT>
 __global__ void __launch_bounds__(256, MINB) k_fused(View<real> v, int N, int zc, KickCoef<real> c)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    fused_tile<real, TY, RX>(v, N, zc, c, blockIdx.x, blockIdx.y, blockIdx.z, smem_raw);
+    fused_tile<real, TY, RX, IT>(v, N, zc, c, blockIdx.x, blockIdx.y, blockIdx.z, smem_raw);
+}
+
+// Diagnostics of the current state through the step's tile walk (tile 32 x 8,
+// nothing written back); one DiagPartial per CTA.
+template <typename real, typename IT>
+__global__ void __launch_bounds__(256) k_fused_diag(View<real> v, int N, int zc, DiagArgs da)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const KickCoef<real> c{};
+    fused_tile<real, 8, 1, IT, MODE_DIAG>(v, N, zc, c, blockIdx.x, blockIdx.y, blockIdx.z, smem_raw, &da);
 }
 
 // Batched fused step: persistent CTAs take (lattice, tile) work items from a
@@ -346,7 +527,7 @@ k_fused_batch(const BatchLattice *lat, BatchState *state, const int2 *items, con
         v.ophr = B.F.phr[o]; v.ophi = B.F.phi[o];
         v.oth1 = B.F.th[o][0]; v.oth2 = B.F.th[o][1]; v.oth3 = B.F.th[o][2];
         const int bx = local % B.tiles_x, by = (local / B.tiles_x) % B.tiles_y, bz = local / (B.tiles_x * B.tiles_y);
-        fused_tile<float, TY, RX>(v, B.N, B.zc, B.coefs[step], bx, by, bz, smem_raw);
+        fused_tile<float, TY, RX, int>(v, B.N, B.zc, B.coefs[step], bx, by, bz, smem_raw);
         __syncthreads();
     }
 }
@@ -383,10 +564,14 @@ cudaError_t launch_shape(const View<real> &v, int N, const KickCoef<real> &c, in
 {
     using G = Geo<real, TY, RX>;
     if (RX > 1 && (N & 1)) return cudaErrorInvalidValue;
+    const bool idx32 = (long long)N * N * N < (1LL << 31);
     static bool configured = false;   // once per instantiation
     if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(k_fused<real, TY, RX, MINB>,
+        cudaError_t e = cudaFuncSetAttribute(k_fused<real, TY, RX, MINB, int>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::smem);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_fused<real, TY, RX, MINB, long long>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::smem);
         if (e != cudaSuccess) return e;
         configured = true;
     }
@@ -396,7 +581,8 @@ cudaError_t launch_shape(const View<real> &v, int N, const KickCoef<real> &c, in
     nch = max(1, min(nch, N / min_chunk));
     const int zc = (N + nch - 1) / nch;
     nch = (N + zc - 1) / zc;
-    k_fused<real, TY, RX, MINB><<<dim3(tx, ty, nch), G::NT, G::smem, st>>>(v, N, zc, c);
+    if (idx32) k_fused<real, TY, RX, MINB, int><<<dim3(tx, ty, nch), G::NT, G::smem, st>>>(v, N, zc, c);
+    else k_fused<real, TY, RX, MINB, long long><<<dim3(tx, ty, nch), G::NT, G::smem, st>>>(v, N, zc, c);
     return cudaGetLastError();
 }
 
@@ -448,6 +634,50 @@ cudaError_t launch_fused_step<double>(const View<double> &v, int N, const KickCo
     }
 }
 
+
+// ---- diagnostics through the fused tile ----
+namespace {
+template <typename real, typename IT>
+cudaError_t launch_diag_it(const View<real> &v, int N, const DiagArgs &da, cudaStream_t st)
+{
+    using G = Geo<real, 8, 1>;
+    if (G::smem > 48 * 1024) {
+        const cudaError_t e = cudaFuncSetAttribute(k_fused_diag<real, IT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                   (int)G::smem);
+        if (e != cudaSuccess) return e;
+    }
+    int tx, ty, nch, zc;
+    fused_diag_grid(N, &tx, &ty, &nch, &zc);
+    k_fused_diag<real, IT><<<dim3(tx, ty, nch), 256, G::smem, st>>>(v, N, zc, da);
+    return cudaGetLastError();
+}
+}  // namespace
+
+void fused_diag_grid(int N, int *tx, int *ty, int *nch, int *zc)
+{
+    *tx = (N + 31) / 32;
+    *ty = (N + 7) / 8;
+    int n = (int)((152LL * 16 + (long long)*tx * *ty - 1) / ((long long)*tx * *ty));
+    n = max(1, min(n, N / 16));
+    *zc = (N + n - 1) / n;
+    *nch = (N + *zc - 1) / *zc;
+}
+
+int fused_diag_ctas(int N)
+{
+    int tx, ty, nch, zc;
+    fused_diag_grid(N, &tx, &ty, &nch, &zc);
+    return tx * ty * nch;
+}
+
+template <typename real>
+cudaError_t launch_fused_diag(const View<real> &v, int N, const DiagArgs &da, cudaStream_t st)
+{
+    return (long long)N * N * N < (1LL << 31) ? launch_diag_it<real, int>(v, N, da, st)
+                                              : launch_diag_it<real, long long>(v, N, da, st);
+}
+template cudaError_t launch_fused_diag<float>(const View<float> &, int, const DiagArgs &, cudaStream_t);
+template cudaError_t launch_fused_diag<double>(const View<double> &, int, const DiagArgs &, cudaStream_t);
 
 // ---- batched step ----
 namespace {

@@ -46,7 +46,6 @@ WORKLOADS = {
 DEFAULT = "lattice1024_fp32_matter_s1"
 BYTES_PER_SITE = {0: 80, 1: 160}      # one read + one write of the 10-real state
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "fused_step_traffic.json")
-TRAFFIC_VARIANT = "ty16_b2"           # shape the committed DRAM-traffic capture was taken on
 
 
 def parse():
@@ -85,14 +84,14 @@ def source_hash(path):
         return hashlib.sha256(f.read()).hexdigest()[:16]
 
 
-def traffic_per_launch(n_sites):
+def traffic_per_launch(n_sites, variant):
     """DRAM bytes per launch of the fused step from the committed ncu summary, if it
-    was taken on the current kernel source."""
+    was taken on the current kernel source and on the shape that ran."""
     try:
         with open(TRAFFIC_FILE) as f:
             d = json.load(f)
         src = os.path.join(ROOT, "paper_1809_00995_gb300", "csrc", "k_fused.cu")
-        if d.get("k_fused_sha256_16") != source_hash(src):
+        if d.get("k_fused_sha256_16") != source_hash(src) or d.get("variant") != variant:
             return None
         return d["dram_bytes_per_site"] * n_sites
     except Exception:
@@ -373,28 +372,47 @@ def main():
         t_max = float(tt.item())
     value = world * n_sites * diag_every * a.steps / (t_max / 1e3)
 
-    # end to end through the public C ABI: host-side timing, synchronous
-    # observables copied to a host struct every bench step
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for _ in range(a.steps):
-        ah.ah_step(g.h, diag_every)
-        obs_e2e = ah.ah_observables(g.h)
-    t_e2e = time.perf_counter() - t0
-    e2e_value = world * n_sites * diag_every * a.steps / t_e2e
+    variant_name = info["variant_name"]
+    g.close()
+
+    # end to end through the public C ABI, host clock: one whole job as a user
+    # runs it -- ah_create_ex from a host ah_config (device allocation, Philox
+    # initial state), then per bench step ah_step(diag_every) and
+    # ah_observables into a host ah_obs (device-to-host copy, stream sync),
+    # then ah_destroy.  The state stays resident between steps, so no step has
+    # host-to-device input bytes; the job's only input is the config.
     import ctypes
+    torch.cuda.synchronize()
+    barrier()
+    t0 = time.perf_counter()
+    cfg_e2e = ah.config(N, precision=prec, kernel=ah.AH_KERNEL_FUSED, era=era, s=s, seed=seed + 1000 * rank,
+                        flags=0 if a.variant else ah.AH_FLAG_AUTOTUNE)
+    h = ah.ah_create_ex(cfg_e2e)
+    try:
+        if a.variant:
+            ah.ah_set_variant(h, names[a.variant])
+        for _ in range(a.steps):
+            ah.ah_step(h, diag_every)
+            obs_e2e = ah.ah_observables(h)
+    finally:
+        ah.ah_destroy(h)
+    t_e2e = time.perf_counter() - t0
+    if dist:
+        tt = torch.tensor([t_e2e], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_e2e = float(tt.item())
+    e2e_value = world * n_sites * diag_every * a.steps / t_e2e
     d2h = ctypes.sizeof(ah.ah_obs)
     final_obs = obs_e2e
-    g.close()
 
     avg_launch_s = step_ms / 1e3 / (a.steps * diag_every)
     alg_bytes = BYTES_PER_SITE[prec] * n_sites
     peak, peak_src = peaks()
     achieved = alg_bytes / avg_launch_s / 1e9
-    tr = traffic_per_launch(n_sites)
+    tr = traffic_per_launch(n_sites, variant_name)
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": tr if info["variant_name"] == TRAFFIC_VARIANT else None,
-                "kernel": "fused step, shape %s (one leapfrog step)" % info["variant_name"], "peak_source": peak_src,
+                "traffic": tr,
+                "kernel": "fused step, shape %s (one leapfrog step)" % variant_name, "peak_source": peak_src,
                 "alg_bytes_per_launch": alg_bytes, "avg_launch_ms": avg_launch_s * 1e3,
                 "step_share_of_time": step_ms / t_ms}
 
@@ -446,7 +464,9 @@ def main():
             "cpu_baseline": cpu,
             "plain_fp64": plain,
             "e2e": {"value": e2e_value, "unit": "site-updates/s", "h2d_bytes_per_step": 0,
-                    "d2h_bytes_per_step": d2h},
+                    "d2h_bytes_per_step": d2h, "h2d_bytes_per_job": ctypes.sizeof(ah.ah_config),
+                    "timed": "ah_create_ex + %d x (ah_step(%d) + ah_observables to host) + ah_destroy, host clock"
+                             % (a.steps, diag_every)},
             "gpu_launches": a.steps * (diag_every * info["step_launches"] + 3),
             "batch": batch,
             "serve": serve,

@@ -222,12 +222,10 @@ __device__ __forceinline__ void fused_tile(const View<real> &v, int N, int zc, c
         for (int t = 0; t <= NS; ++t) {
             if (t < NS || has_halo) {
                 const int e = t < NS ? eix(t) : heix;
+                real sn[3], co[3];
+                sincos_link3(fth[t], sn, co);
 #pragma unroll
-                for (int d = 0; d < 3; ++d) {
-                    real sn, co;
-                    sincos_link(fth[t][d], &sn, &co);
-                    sU[(b * 3 + d) * NE + e] = { co, sn };
-                }
+                for (int d = 0; d < 3; ++d) sU[(b * 3 + d) * NE + e] = { co[d], sn[d] };
                 sF[b * NE + e] = { fph[t][0], fph[t][1] };
             }
         }

@@ -13,6 +13,23 @@
 
 namespace ah {
 
+// sin r, cos r on |r| <= pi/4 (the polynomials above)
+__device__ __forceinline__ void sincos_poly(float r, float *s, float *c)
+{
+    const float r2 = r * r;
+    // sin r = r + r^3 (-1/3! + r^2 (1/5! + r^2 (-1/7! + r^2 / 9!)))
+    float ps = fmaf(r2, 2.755731884e-06f, -1.984127011e-04f);
+    ps = fmaf(r2, ps, 8.333333768e-03f);
+    ps = fmaf(r2, ps, -1.666666716e-01f);
+    *s = fmaf(r * r2, ps, r);
+    // cos r = 1 + r^2 (-1/2! + r^2 (1/4! + r^2 (-1/6! + r^2 (1/8! - r^2 / 10!))))
+    float pc = fmaf(r2, -2.755731998e-07f, 2.480158764e-05f);
+    pc = fmaf(r2, pc, -1.388888923e-03f);
+    pc = fmaf(r2, pc, 4.166666791e-02f);
+    pc = fmaf(r2, pc, -0.5f);
+    *c = fmaf(r2, pc, 1.0f);
+}
+
 __device__ __forceinline__ void sincos_link(float t, float *s, float *c)
 {
     if (!(fabsf(t) < 131072.0f)) {
@@ -23,18 +40,8 @@ __device__ __forceinline__ void sincos_link(float t, float *s, float *c)
     float r = fmaf(-kf, 0x1.921fb6p+0f, t);               // P1
     r = fmaf(-kf, -0x1.777a5cp-25f, r);                   // P2
     r = fmaf(-kf, -0x1.ee59dap-50f, r);                   // P3
-    const float r2 = r * r;
-    // sin r = r + r^3 (-1/3! + r^2 (1/5! + r^2 (-1/7! + r^2 / 9!)))
-    float ps = fmaf(r2, 2.755731884e-06f, -1.984127011e-04f);
-    ps = fmaf(r2, ps, 8.333333768e-03f);
-    ps = fmaf(r2, ps, -1.666666716e-01f);
-    const float sr = fmaf(r * r2, ps, r);
-    // cos r = 1 + r^2 (-1/2! + r^2 (1/4! + r^2 (-1/6! + r^2 (1/8! - r^2 / 10!))))
-    float pc = fmaf(r2, -2.755731998e-07f, 2.480158764e-05f);
-    pc = fmaf(r2, pc, -1.388888923e-03f);
-    pc = fmaf(r2, pc, 4.166666791e-02f);
-    pc = fmaf(r2, pc, -0.5f);
-    const float cr = fmaf(r2, pc, 1.0f);
+    float sr, cr;
+    sincos_poly(r, &sr, &cr);
     const int q = (int)kf;
     const float a = (q & 1) ? cr : sr;        // |sin t|
     const float b = (q & 1) ? sr : cr;        // |cos t|
@@ -42,6 +49,27 @@ __device__ __forceinline__ void sincos_link(float t, float *s, float *c)
     *c = ((q + 1) & 2) ? -b : b;
 }
 
+// The three links of a site.  When every active lane of the warp has all three
+// phases in [-0.78, 0.78] the reduction is the identity (k = 0, r = t exactly)
+// and the quadrant step selects (sin r, cos r), so the polynomials alone give
+// the same bits as sincos_link; the test is one warp vote.
+__device__ __forceinline__ void sincos_link3(const float t[3], float s[3], float c[3])
+{
+    const float m = fmaxf(fabsf(t[0]), fmaxf(fabsf(t[1]), fabsf(t[2])));
+    if (__all_sync(__activemask(), m <= 0.78f)) {        // 0.78 * 2/pi < 1/2: k = 0
+#pragma unroll
+        for (int d = 0; d < 3; ++d) sincos_poly(t[d], &s[d], &c[d]);
+    } else {
+#pragma unroll
+        for (int d = 0; d < 3; ++d) sincos_link(t[d], &s[d], &c[d]);
+    }
+}
+
 __device__ __forceinline__ void sincos_link(double t, double *s, double *c) { sincos(t, s, c); }
+__device__ __forceinline__ void sincos_link3(const double t[3], double s[3], double c[3])
+{
+#pragma unroll
+    for (int d = 0; d < 3; ++d) sincos(t[d], &s[d], &c[d]);
+}
 
 }  // namespace ah

@@ -67,10 +67,17 @@ enum { AH_KERNEL_AUTO = 0, AH_KERNEL_PLAIN = 1, AH_KERNEL_FUSED = 2 };
  *  precision (accumulated in FP64), the Gauss residual in FP64, and windings by
  *  sign carries that equal the FP64 arctangent formula, with the plaquettes
  *  near a branch cut re-evaluated in FP64. */
-enum { AH_FLAG_EXACT_DIAG = 1, AH_FLAG_AUTOTUNE = 2 };
+enum { AH_FLAG_EXACT_DIAG = 1, AH_FLAG_AUTOTUNE = 2, AH_FLAG_WRAP_THETA = 4 };
 /* AUTOTUNE: at creation, time every compile-time shape of the fused step on
  * the initial state (then re-initialise it) and keep the fastest; results are
- * cached per (device, N, precision) for the life of the process. */
+ * cached per (device, N, precision) for the life of the process.
+ * WRAP_THETA: after every drift (Eq. up_A) a link phase with |theta| > pi is
+ * replaced by theta - 2 pi k, k the nearest integer to theta / 2 pi, so that
+ * theta stays in [-pi, pi] (to one rounding) and an FP32 state keeps its
+ * absolute resolution on theta at late times.  U = e^{i theta}, the
+ * plaquettes and every observable except max |theta| are unchanged up to
+ * rounding; ah_get_fields returns the wrapped phases.  Without the flag theta
+ * is non-compact (never wrapped), as in Eq. up_A. */
 
 typedef struct ah_config {
     int32_t N;            /* lattice side, 4 <= N <= 2048                         */

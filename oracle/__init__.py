@@ -46,7 +46,7 @@ def build(force: bool = False) -> str:
 
 class _Params(ctypes.Structure):
     _fields_ = [("N", ctypes.c_int64), ("dx", ctypes.c_double), ("dt", ctypes.c_double),
-                ("era", ctypes.c_int32), ("pad_", ctypes.c_int32), ("s", ctypes.c_double),
+                ("era", ctypes.c_int32), ("wrap_theta", ctypes.c_int32), ("s", ctypes.c_double),
                 ("lambda0", ctypes.c_double), ("e0", ctypes.c_double), ("sigma", ctypes.c_double),
                 ("tau0", ctypes.c_double), ("tau_ref", ctypes.c_double), ("seed", ctypes.c_uint64)]
 
@@ -105,6 +105,7 @@ class Params:
     tau0: float = 1.0
     tau_ref: float | None = None   # default: tau_end = N dx / 2
     seed: int = 1
+    wrap_theta: bool = False       # compact link phases: theta kept in [-pi, pi]
 
     @property
     def tau_end(self) -> float:
@@ -112,7 +113,7 @@ class Params:
 
     def c(self) -> _Params:
         tr = self.tau_end if self.tau_ref is None else self.tau_ref
-        return _Params(self.N, self.dx, self.dt, self.era, 0, self.s, self.lambda0, self.e0,
+        return _Params(self.N, self.dx, self.dt, self.era, int(self.wrap_theta), self.s, self.lambda0, self.e0,
                        self.sigma, self.tau0, tr, self.seed)
 
 

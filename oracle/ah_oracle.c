@@ -36,7 +36,7 @@ typedef struct {
     int64_t N;        /* side of the global periodic lattice (Philox counters) */
     double dx, dt;    /* lattice spacing Delta x, time step Delta eta */
     int32_t era;      /* 0 Minkowski (a=1), 1 radiation (a ~ tau), 2 matter (a ~ tau^2) */
-    int32_t pad_;
+    int32_t wrap_theta; /* nonzero: theta reduced to [-pi, pi] after each drift */
     double s;         /* coupling exponent of Eq. 7 */
     double lambda0, e0, sigma;
     double tau0;      /* conformal time at step 0 */
@@ -227,9 +227,20 @@ static void kicks(const aho_params *p, const double *f, int64_t M, int64_t n,
             }
 }
 
+/* A link phase only enters through U = e^{i theta}, so theta and theta - 2 pi k
+ * describe the same configuration: the compact reading keeps theta in
+ * [-pi, pi] by subtracting 2 pi times the nearest integer to theta / 2 pi
+ * whenever |theta| > pi. */
+static double wrap_phase(double t)
+{
+    const double two_pi = 6.283185307179586476925287;
+    if (fabs(t) > 0.5 * two_pi) t -= two_pi * nearbyint(t / two_pi);
+    return t;
+}
+
 /* One leapfrog step n -> n+1 (Eqs. up_pi, up_E, up_phi, up_A): both kicks
  * read only step-n data, then phi += dt Pi^{n+1/2}, theta += dt E^{n+1/2}.
- * theta is kept non-compact (never wrapped). */
+ * theta is non-compact (never wrapped) unless p->wrap_theta is set. */
 int aho_step(const aho_params *p, double *f, int64_t M, int64_t n)
 {
     const int64_t M3 = M * M * M;
@@ -244,7 +255,10 @@ int aho_step(const aho_params *p, double *f, int64_t M, int64_t n)
         for (int d = 0; d < 3; ++d) f[(EL + d) * M3 + s] = e_new[d * M3 + s];
         f[PHR * M3 + s] += p->dt * pi_new[s];
         f[PHI * M3 + s] += p->dt * pi_new[M3 + s];
-        for (int d = 0; d < 3; ++d) f[(TH + d) * M3 + s] += p->dt * e_new[d * M3 + s];
+        for (int d = 0; d < 3; ++d) {
+            f[(TH + d) * M3 + s] += p->dt * e_new[d * M3 + s];
+            if (p->wrap_theta) f[(TH + d) * M3 + s] = wrap_phase(f[(TH + d) * M3 + s]);
+        }
     }
     free(pi_new);
     free(e_new);

@@ -76,6 +76,7 @@ KickCoef<real> kick_coef(const ah_config &c, int64_t n)
     k.c_curl = (real)(c.dt * idx2 * (ep / en) * (ep / en));
     k.dt = (real)c.dt;
     k.sigma2 = (real)(c.sigma * c.sigma);
+    k.wrap = (c.flags & AH_FLAG_WRAP_THETA) != 0;
     return k;
 }
 
@@ -171,7 +172,8 @@ ah_status validate(const ah_config &c)
         return fail(AH_ERR_ARG, "unknown precision %d", c.precision);
     if (c.kernel < AH_KERNEL_AUTO || c.kernel > AH_KERNEL_FUSED)
         return fail(AH_ERR_ARG, "unknown kernel %d", c.kernel);
-    if (c.flags & ~(AH_FLAG_EXACT_DIAG | AH_FLAG_AUTOTUNE)) return fail(AH_ERR_ARG, "unknown flags 0x%x", c.flags);
+    if (c.flags & ~(AH_FLAG_EXACT_DIAG | AH_FLAG_AUTOTUNE | AH_FLAG_WRAP_THETA))
+        return fail(AH_ERR_ARG, "unknown flags 0x%x", c.flags);
     if (!std::isfinite(c.s)) return fail(AH_ERR_ARG, "s must be finite");
     if (c.era != AH_MINKOWSKI && !(c.tau0 > 0)) return fail(AH_ERR_ARG, "tau0 must be > 0");
     if (!(c.tau_ref > 0)) return fail(AH_ERR_ARG, "tau_ref must be > 0");

@@ -37,7 +37,30 @@ struct View {
 template <typename real>
 struct KickCoef {
     real c_damp, c_pot, c_lap, c_edamp, c_cur, c_curl, dt, sigma2;
+    int wrap;    // AH_FLAG_WRAP_THETA: reduce theta to [-pi, pi] after the drift
 };
+
+// theta - 2 pi k with k the nearest integer to theta / 2 pi, when |theta| > pi;
+// 2 pi is split into its nearest value in the type plus the remainder, so
+// the subtraction is accurate to the last bit of the result.
+__device__ __forceinline__ float wrap_phase(float t)
+{
+    if (fabsf(t) > 3.14159265f) {
+        const float k = rintf(t * 0.159154943f);
+        t = fmaf(-k, 6.28318548f, t);                 // fl(2 pi)
+        t = fmaf(-k, -1.74845553e-7f, t);             // 2 pi - fl(2 pi)
+    }
+    return t;
+}
+__device__ __forceinline__ double wrap_phase(double t)
+{
+    if (fabs(t) > 3.141592653589793) {
+        const double k = rint(t * 0.15915494309189535);
+        t = fma(-k, 6.283185307179586, t);            // fl(2 pi)
+        t = fma(-k, 2.4492935982947064e-16, t);       // 2 pi - fl(2 pi)
+    }
+    return t;
+}
 
 // Per-site diagnostic coefficients at step n (FP64 always).
 struct DiagCoef {

@@ -447,6 +447,11 @@ __device__ __forceinline__ void fused_tile(const View<real> &v, int N, int zc, c
             o_t1[m] = th_0[m][0] + c.dt * ne1;
             o_t2[m] = th_0[m][1] + c.dt * ne2;
             o_t3[m] = th_0[m][2] + c.dt * ne3;
+            if (c.wrap) {
+                o_t1[m] = wrap_phase(o_t1[m]);
+                o_t2[m] = wrap_phase(o_t2[m]);
+                o_t3[m] = wrap_phase(o_t3[m]);
+            }
             // march: plane z becomes z-1
             if constexpr (DIAG) e3_m[m] = e3[m];
             ph_m[m] = f0;

@@ -242,7 +242,12 @@ k_pair(View<float> v, int N, int zc, KickCoef<float> c)
             const float2 ne3 = fma2(f2(-c.c_curl), cl3, fma2(f2(c.c_edamp), e3, mul2(f2(c.c_cur), cu3)));
             const float2 dt = f2(c.dt);
             const float2 ofr = fma2(dt, npr, f0.r), ofi = fma2(dt, npi, f0.i);
-            const float2 ot1 = fma2(dt, ne1, th_a1), ot2 = fma2(dt, ne2, th_a2), ot3 = fma2(dt, ne3, th_a3);
+            float2 ot1 = fma2(dt, ne1, th_a1), ot2 = fma2(dt, ne2, th_a2), ot3 = fma2(dt, ne3, th_a3);
+            if (c.wrap) {
+                ot1 = make_float2(wrap_phase(ot1.x), wrap_phase(ot1.y));
+                ot2 = make_float2(wrap_phase(ot2.x), wrap_phase(ot2.y));
+                ot3 = make_float2(wrap_phase(ot3.x), wrap_phase(ot3.y));
+            }
             const long long s = base + rowoff;
             if (okx && oky) {
                 stg2(v.pir + s, npr); stg2(v.pii + s, npi);

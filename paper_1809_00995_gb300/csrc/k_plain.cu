@@ -113,17 +113,20 @@ __global__ void __launch_bounds__(BX * BY) k_kick_e(View<real> v, int N, KickCoe
     }
 }
 
-// stepC: phi += dt Pi^{n+1/2}, theta += dt E^{n+1/2} (Eqs. up_phi, up_A).
+// stepC: phi += dt Pi^{n+1/2}, theta += dt E^{n+1/2} (Eqs. up_phi, up_A),
+// theta reduced to [-pi, pi] when wrap is set.
 template <typename real>
-__global__ void __launch_bounds__(256) k_drift(View<real> v, long long nsites, real dt)
+__global__ void __launch_bounds__(256) k_drift(View<real> v, long long nsites, real dt, int wrap)
 {
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x; s < nsites; s += stride) {
         v.ophr[s] = v.phr[s] + dt * v.pir[s];
         v.ophi[s] = v.phi[s] + dt * v.pii[s];
-        v.oth1[s] = v.th1[s] + dt * v.e1[s];
-        v.oth2[s] = v.th2[s] + dt * v.e2[s];
-        v.oth3[s] = v.th3[s] + dt * v.e3[s];
+        real t1 = v.th1[s] + dt * v.e1[s], t2 = v.th2[s] + dt * v.e2[s], t3 = v.th3[s] + dt * v.e3[s];
+        if (wrap) { t1 = wrap_phase(t1); t2 = wrap_phase(t2); t3 = wrap_phase(t3); }
+        v.oth1[s] = t1;
+        v.oth2[s] = t2;
+        v.oth3[s] = t3;
     }
 }
 
@@ -138,7 +141,7 @@ cudaError_t launch_plain_step(const View<real> &v, int N, const KickCoef<real> &
     const long long ns = (long long)N * N * N;
     long long g = (ns + 255) / 256;
     if (g > 152LL * 32) g = 152LL * 32;
-    k_drift<real><<<(int)g, 256, 0, st>>>(v, ns, c.dt);
+    k_drift<real><<<(int)g, 256, 0, st>>>(v, ns, c.dt, c.wrap);
     return cudaGetLastError();
 }
 

@@ -282,9 +282,11 @@ k_fused_tma(const __grid_constant__ TmaMaps maps, View<float> v, int N, int zc, 
                 v.e1[s] = ne1; v.e2[s] = ne2; v.e3[s] = ne3;
                 v.ophr[s] = f0.r + c.dt * npr;
                 v.ophi[s] = f0.i + c.dt * npi;
-                v.oth1[s] = th_a[0] + c.dt * ne1;
-                v.oth2[s] = th_a[1] + c.dt * ne2;
-                v.oth3[s] = th_a[2] + c.dt * ne3;
+                float t1 = th_a[0] + c.dt * ne1, t2 = th_a[1] + c.dt * ne2, t3 = th_a[2] + c.dt * ne3;
+                if (c.wrap) { t1 = wrap_phase(t1); t2 = wrap_phase(t2); t3 = wrap_phase(t3); }
+                v.oth1[s] = t1;
+                v.oth2[s] = t2;
+                v.oth3[s] = t3;
             }
             ph_m = f0;
             u3_m = u3;

@@ -54,3 +54,15 @@ def test_config_defaults_without_gpu():
     c = ah.ah_config_default(64)
     assert (c.N, c.era, c.precision, c.dx, c.dt, c.lambda0, c.e0, c.sigma) == (64, 1, 0, 0.5, 0.1, 2.0, 1.0, 1.0)
     assert c.tau_end == 16.0 and c.tau_ref == 16.0 and c.tau0 == 1.0
+
+
+def test_binding_constants_match_the_header():
+    """Every enum constant of include/ah.h has the same value in the binding."""
+    import re
+    hdr = open(HEADER).read()
+    found = 0
+    for body in re.findall(r"enum\s*(?:\w+\s*)?\{([^}]*)\}", hdr):
+        for name, val in re.findall(r"(AH_\w+)\s*=\s*(\d+)", body):
+            assert getattr(ah, name) == int(val), name
+            found += 1
+    assert found >= 20 and ah.AH_FLAG_WRAP_THETA == 4

@@ -443,3 +443,36 @@ def test_stress_energy_special_cases():
     g[7:10] = 0.0
     o = O.observables(pv, g, 0)                         # at rest: L = -rho
     assert abs(o["sum_L"] + o["sum_rho"]) < 1e-12 * o["sum_rho"]
+
+
+# ---------------------------------------------------------------- compact theta
+def test_wrapped_theta_is_the_same_evolution_mod_2pi():
+    """theta only enters through e^{i theta}: evolving with theta reduced to
+    [-pi, pi] after every drift gives the non-compact evolution's phi, Pi, E
+    (to rounding) and its theta modulo 2 pi, with every phase inside [-pi, pi].
+    A reduction by pi, of the wrong component, or with the wrong sign breaks it."""
+    N = 6
+    f = random_state(N, 31, th_amp=9.0, e_amp=2.0)      # phases far outside [-pi, pi]
+    a = O.Params(N=N, era=O.MINKOWSKI, seed=1)
+    b = O.Params(N=N, era=O.MINKOWSKI, seed=1, wrap_theta=True)
+    fa, fb = f.copy(), f.copy()
+    O.evolve(a, fa, 0, 25)
+    O.evolve(b, fb, 0, 25)
+    assert np.max(np.abs(fb[4:7])) <= np.pi * (1 + 1e-15)
+    assert np.max(np.abs(fa[4:7])) > 3 * np.pi
+    for c in (0, 1, 2, 3, 7, 8, 9):
+        assert np.max(np.abs(fa[c] - fb[c])) <= 1e-11 * max(1.0, np.max(np.abs(fa[c]))), c
+    d = np.remainder(fa[4:7] - fb[4:7] + np.pi, 2 * np.pi) - np.pi
+    assert np.max(np.abs(d)) < 1e-11
+    # every other observable agrees; max |theta| is the one that changes
+    oa, ob = O.observables(a, fa, 25), O.observables(b, fb, 25)
+    for k in ("sum_L", "sum_rho", "sum_p", "sum_B", "sum_gauss2"):
+        assert abs(oa[k] - ob[k]) <= 1e-10 * max(1.0, abs(oa[k])), k
+    assert oa["sum_abs_W"] == ob["sum_abs_W"]
+    assert ob["max_abs_theta"] <= np.pi * (1 + 1e-15) < oa["max_abs_theta"]
+    # phases already inside [-pi, pi] are left bit for bit as they are
+    g = random_state(N, 32, th_amp=0.5, e_amp=0.05)
+    ga, gb = g.copy(), g.copy()
+    O.evolve(a, ga, 0, 3)
+    O.evolve(b, gb, 0, 3)
+    assert np.array_equal(ga, gb)

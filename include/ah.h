@@ -67,7 +67,7 @@ enum { AH_KERNEL_AUTO = 0, AH_KERNEL_PLAIN = 1, AH_KERNEL_FUSED = 2 };
  *  precision (accumulated in FP64), the Gauss residual in FP64, and windings by
  *  sign carries that equal the FP64 arctangent formula, with the plaquettes
  *  near a branch cut re-evaluated in FP64. */
-enum { AH_FLAG_EXACT_DIAG = 1, AH_FLAG_AUTOTUNE = 2, AH_FLAG_WRAP_THETA = 4 };
+enum { AH_FLAG_EXACT_DIAG = 1, AH_FLAG_AUTOTUNE = 2, AH_FLAG_WRAP_THETA = 4, AH_FLAG_CORE_GROWTH = 8 };
 /* AUTOTUNE: at creation, time every compile-time shape of the fused step on
  * the initial state (then re-initialise it) and keep the fastest; results are
  * cached per (device, N, precision) for the life of the process.
@@ -77,7 +77,13 @@ enum { AH_FLAG_EXACT_DIAG = 1, AH_FLAG_AUTOTUNE = 2, AH_FLAG_WRAP_THETA = 4 };
  * absolute resolution on theta at late times.  U = e^{i theta}, the
  * plaquettes and every observable except max |theta| are unchanged up to
  * rounding; ah_get_fields returns the wrapped phases.  Without the flag theta
- * is non-compact (never wrapped), as in Eq. up_A. */
+ * is non-compact (never wrapped), as in Eq. up_A.
+ * CORE_GROWTH: the schedule of Sec. 2 that grows the comoving string width
+ * first and then evolves the true equations: the exponent of Eq. 7 is s for
+ * tau < tau_ref (s < 0 grows the width) and 1 from tau_ref on.  Since
+ * a(tau_ref) = 1, e and lambda equal e0 and lambda0 on both sides of the
+ * switch, so the couplings are continuous there.  Every coupling of a step
+ * (at tau_n and tau_n +- dt/2) takes the exponent of its own time. */
 
 typedef struct ah_config {
     int32_t N;            /* lattice side, 4 <= N <= 2048                         */

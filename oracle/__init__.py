@@ -46,7 +46,7 @@ def build(force: bool = False) -> str:
 
 class _Params(ctypes.Structure):
     _fields_ = [("N", ctypes.c_int64), ("dx", ctypes.c_double), ("dt", ctypes.c_double),
-                ("era", ctypes.c_int32), ("wrap_theta", ctypes.c_int32), ("s", ctypes.c_double),
+                ("era", ctypes.c_int32), ("flags", ctypes.c_int32), ("s", ctypes.c_double),
                 ("lambda0", ctypes.c_double), ("e0", ctypes.c_double), ("sigma", ctypes.c_double),
                 ("tau0", ctypes.c_double), ("tau_ref", ctypes.c_double), ("seed", ctypes.c_uint64)]
 
@@ -106,6 +106,7 @@ class Params:
     tau_ref: float | None = None   # default: tau_end = N dx / 2
     seed: int = 1
     wrap_theta: bool = False       # compact link phases: theta kept in [-pi, pi]
+    core_growth: bool = False      # exponent s before tau_ref, 1 from tau_ref on (Eq. 7)
 
     @property
     def tau_end(self) -> float:
@@ -113,7 +114,8 @@ class Params:
 
     def c(self) -> _Params:
         tr = self.tau_end if self.tau_ref is None else self.tau_ref
-        return _Params(self.N, self.dx, self.dt, self.era, int(self.wrap_theta), self.s, self.lambda0, self.e0,
+        flags = (1 if self.wrap_theta else 0) | (2 if self.core_growth else 0)
+        return _Params(self.N, self.dx, self.dt, self.era, flags, self.s, self.lambda0, self.e0,
                        self.sigma, self.tau0, tr, self.seed)
 
 

@@ -36,7 +36,8 @@ typedef struct {
     int64_t N;        /* side of the global periodic lattice (Philox counters) */
     double dx, dt;    /* lattice spacing Delta x, time step Delta eta */
     int32_t era;      /* 0 Minkowski (a=1), 1 radiation (a ~ tau), 2 matter (a ~ tau^2) */
-    int32_t wrap_theta; /* nonzero: theta reduced to [-pi, pi] after each drift */
+    int32_t flags;    /* bit 0: theta reduced to [-pi, pi] after each drift;
+                         bit 1: core growth (exponent s before tau_ref, 1 after) */
     double s;         /* coupling exponent of Eq. 7 */
     double lambda0, e0, sigma;
     double tau0;      /* conformal time at step 0 */
@@ -101,8 +102,21 @@ double aho_scale_factor(const aho_params *p, double tau)
     if (p->era == 2) return r * r;
     return 1.0;
 }
-static double coupling_e(const aho_params *p, double a) { return p->e0 * pow(a, p->s - 1.0); }
-static double coupling_lambda(const aho_params *p, double a) { return p->lambda0 * pow(a, 2.0 * (p->s - 1.0)); }
+/* Eq. 7.  Under core growth (Sec. 2: the comoving width is grown first, then
+ * the true equations are evolved) the exponent is s before tau_ref and 1 from
+ * tau_ref on; a(tau_ref) = 1 makes both branches give e0 and lambda0 there. */
+static double exponent_s(const aho_params *p, double tau)
+{
+    return ((p->flags & 2) && tau >= p->tau_ref) ? 1.0 : p->s;
+}
+static double coupling_e(const aho_params *p, double a, double tau)
+{
+    return p->e0 * pow(a, exponent_s(p, tau) - 1.0);
+}
+static double coupling_lambda(const aho_params *p, double a, double tau)
+{
+    return p->lambda0 * pow(a, 2.0 * (exponent_s(p, tau) - 1.0));
+}
 /* tau_n = tau0 + n dt, taken from the integer n (never accumulated) */
 double aho_tau(const aho_params *p, int64_t n) { return p->tau0 + (double)n * p->dt; }
 
@@ -177,8 +191,8 @@ static void kicks(const aho_params *p, const double *f, int64_t M, int64_t n,
     const double dt = p->dt, dx = p->dx, sig2 = p->sigma * p->sigma;
     const double tn = aho_tau(p, n), tm = tn - 0.5 * dt, tp = tn + 0.5 * dt;
     const double an = aho_scale_factor(p, tn), am = aho_scale_factor(p, tm), ap = aho_scale_factor(p, tp);
-    const double en = coupling_e(p, an), em = coupling_e(p, am), ep = coupling_e(p, ap);
-    const double lam_n = coupling_lambda(p, an);
+    const double en = coupling_e(p, an, tn), em = coupling_e(p, am, tm), ep = coupling_e(p, ap, tp);
+    const double lam_n = coupling_lambda(p, an, tn);
 
 #pragma omp parallel for schedule(static)
     for (int64_t z = 0; z < M; ++z)
@@ -240,7 +254,7 @@ static double wrap_phase(double t)
 
 /* One leapfrog step n -> n+1 (Eqs. up_pi, up_E, up_phi, up_A): both kicks
  * read only step-n data, then phi += dt Pi^{n+1/2}, theta += dt E^{n+1/2}.
- * theta is non-compact (never wrapped) unless p->wrap_theta is set. */
+ * theta is non-compact (never wrapped) unless flag bit 0 is set. */
 int aho_step(const aho_params *p, double *f, int64_t M, int64_t n)
 {
     const int64_t M3 = M * M * M;
@@ -257,7 +271,7 @@ int aho_step(const aho_params *p, double *f, int64_t M, int64_t n)
         f[PHI * M3 + s] += p->dt * pi_new[M3 + s];
         for (int d = 0; d < 3; ++d) {
             f[(TH + d) * M3 + s] += p->dt * e_new[d * M3 + s];
-            if (p->wrap_theta) f[(TH + d) * M3 + s] = wrap_phase(f[(TH + d) * M3 + s]);
+            if (p->flags & 1) f[(TH + d) * M3 + s] = wrap_phase(f[(TH + d) * M3 + s]);
         }
     }
     free(pi_new);
@@ -346,8 +360,8 @@ void aho_diag(const aho_params *p, const double *f, int64_t M, int64_t n,
     const double dx = p->dx, sig2 = p->sigma * p->sigma;
     const double tn = aho_tau(p, n), tm = tn - 0.5 * p->dt;
     const double an = aho_scale_factor(p, tn), am = aho_scale_factor(p, tm);
-    const double en = coupling_e(p, an), em = coupling_e(p, am);
-    const double lam_n = coupling_lambda(p, an);
+    const double en = coupling_e(p, an, tn), em = coupling_e(p, am, tm);
+    const double lam_n = coupling_lambda(p, an, tn);
     const double e2a2 = en * en * an * an;
 
     /* per-plane partial sums, combined in plane order: the result does not
@@ -467,8 +481,8 @@ double aho_energy(const aho_params *p, const double *f, int64_t M, int64_t n)
     kicks(p, f, M, n, pi_new, e_new);
     aho_diag_out d;
     aho_diag(p, f, M, n, 0, 0, 0, M, M, M, &d);
-    const double an = aho_scale_factor(p, aho_tau(p, n));
-    const double en = coupling_e(p, an), dx = p->dx;
+    const double tn = aho_tau(p, n), an = aho_scale_factor(p, tn);
+    const double en = coupling_e(p, an, tn), dx = p->dx;
     ksum kin = { 0.0, 0.0 }, el = { 0.0, 0.0 };
     for (int64_t s = 0; s < M3; ++s) {
         double k1 = f[PIR * M3 + s] * f[PIR * M3 + s] + f[PII * M3 + s] * f[PII * M3 + s];

@@ -53,8 +53,16 @@ double scale_factor(const ah_config &c, double tau)
     if (c.era == AH_MATTER) return r * r;
     return 1.0;
 }
-double coupling_e(const ah_config &c, double a) { return c.e0 * std::pow(a, c.s - 1.0); }
-double coupling_lambda(const ah_config &c, double a) { return c.lambda0 * std::pow(a, 2.0 * (c.s - 1.0)); }
+// exponent of Eq. 7 at time tau (AH_FLAG_CORE_GROWTH: s before tau_ref, 1 after)
+double s_at(const ah_config &c, double tau)
+{
+    return (c.flags & AH_FLAG_CORE_GROWTH) && tau >= c.tau_ref ? 1.0 : c.s;
+}
+double coupling_e(const ah_config &c, double a, double tau) { return c.e0 * std::pow(a, s_at(c, tau) - 1.0); }
+double coupling_lambda(const ah_config &c, double a, double tau)
+{
+    return c.lambda0 * std::pow(a, 2.0 * (s_at(c, tau) - 1.0));
+}
 double tau_of(const ah_config &c, int64_t n) { return c.tau0 + (double)n * c.dt; }
 
 // Kick coefficients of step n (Eqs. up_pi, up_E), FP64, half-step scale
@@ -64,8 +72,8 @@ KickCoef<real> kick_coef(const ah_config &c, int64_t n)
 {
     const double tn = tau_of(c, n), tm = tn - 0.5 * c.dt, tp = tn + 0.5 * c.dt;
     const double an = scale_factor(c, tn), am = scale_factor(c, tm), ap = scale_factor(c, tp);
-    const double en = coupling_e(c, an), em = coupling_e(c, am), ep = coupling_e(c, ap);
-    const double lam = coupling_lambda(c, an);
+    const double en = coupling_e(c, an, tn), em = coupling_e(c, am, tm), ep = coupling_e(c, ap, tp);
+    const double lam = coupling_lambda(c, an, tn);
     const double idx2 = 1.0 / (c.dx * c.dx);
     KickCoef<real> k;
     k.c_damp = (real)((am / ap) * (am / ap));
@@ -84,8 +92,8 @@ DiagCoef diag_coef(const ah_config &c, int64_t n)
 {
     const double tn = tau_of(c, n), tm = tn - 0.5 * c.dt;
     const double an = scale_factor(c, tn), am = scale_factor(c, tm);
-    const double en = coupling_e(c, an), em = coupling_e(c, am);
-    const double lam = coupling_lambda(c, an);
+    const double en = coupling_e(c, an, tn), em = coupling_e(c, am, tm);
+    const double lam = coupling_lambda(c, an, tn);
     const double dx2 = c.dx * c.dx, e2a2 = en * en * an * an;
     DiagCoef d;
     d.inv_dx2 = 1.0 / dx2;
@@ -172,7 +180,7 @@ ah_status validate(const ah_config &c)
         return fail(AH_ERR_ARG, "unknown precision %d", c.precision);
     if (c.kernel < AH_KERNEL_AUTO || c.kernel > AH_KERNEL_FUSED)
         return fail(AH_ERR_ARG, "unknown kernel %d", c.kernel);
-    if (c.flags & ~(AH_FLAG_EXACT_DIAG | AH_FLAG_AUTOTUNE | AH_FLAG_WRAP_THETA))
+    if (c.flags & ~(AH_FLAG_EXACT_DIAG | AH_FLAG_AUTOTUNE | AH_FLAG_WRAP_THETA | AH_FLAG_CORE_GROWTH))
         return fail(AH_ERR_ARG, "unknown flags 0x%x", c.flags);
     if (!std::isfinite(c.s)) return fail(AH_ERR_ARG, "s must be finite");
     if (c.era != AH_MINKOWSKI && !(c.tau0 > 0)) return fail(AH_ERR_ARG, "tau0 must be > 0");
@@ -181,9 +189,18 @@ ah_status validate(const ah_config &c)
     if (c.dt * std::sqrt(3.0) > c.dx) return fail(AH_ERR_ARG, "Courant: need dt <= dx/sqrt(3)");
     // Leapfrog stability of the stiffest mode: lattice gradient (12/dx^2) plus the
     // scalar / vector mass terms lambda0 sigma^2 a^2s and 2 e0^2 sigma^2 a^2s, with
-    // a^s largest at one end of [tau0, tau_end].  Require dt^2 w^2 < 0.9 * 4.
-    const double a0 = scale_factor(c, c.tau0), a1 = scale_factor(c, c.tau_end);
-    const double as2 = std::fmax(std::pow(a0, 2.0 * c.s), std::pow(a1, 2.0 * c.s));
+    // a^s largest at one end of [tau0, tau_end] (of each of the two stretches
+    // with their own s under core growth).  Require dt^2 w^2 < 0.9 * 4.
+    auto as2_over = [&c](double t0, double t1, double s) {
+        return std::fmax(std::pow(scale_factor(c, t0), 2.0 * s), std::pow(scale_factor(c, t1), 2.0 * s));
+    };
+    double as2 = 0.0;
+    if (!(c.flags & AH_FLAG_CORE_GROWTH) || c.tau_end < c.tau_ref)
+        as2 = as2_over(c.tau0, c.tau_end, c.s);
+    else if (c.tau0 >= c.tau_ref)
+        as2 = as2_over(c.tau0, c.tau_end, 1.0);
+    else
+        as2 = std::fmax(as2_over(c.tau0, c.tau_ref, c.s), as2_over(c.tau_ref, c.tau_end, 1.0));
     const double m2 = std::fmax(c.lambda0, 2.0 * c.e0 * c.e0) * c.sigma * c.sigma * as2;
     const double w2dt2 = c.dt * c.dt * (12.0 / (c.dx * c.dx) + m2);
     if (!(w2dt2 < 3.6))

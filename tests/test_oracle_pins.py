@@ -476,3 +476,25 @@ def test_wrapped_theta_is_the_same_evolution_mod_2pi():
     O.evolve(a, ga, 0, 3)
     O.evolve(b, gb, 0, 3)
     assert np.array_equal(ga, gb)
+
+
+# ---------------------------------------------------------------- core growth
+def test_core_growth_is_two_runs_joined_at_tau_ref():
+    """Core growth (Sec. 2): exponent s before tau_ref, 1 after.  With tau_ref on a
+    half step, the schedule is exactly an s run up to the step whose upper half
+    time is tau_ref followed by an s = 1 run (a(tau_ref) = 1 gives both branches
+    e0 and lambda0 at the switch), and it differs from either run alone."""
+    N, k, n = 8, 8, 16
+    kw = dict(N=N, era=O.RADIATION, dt=0.125, tau0=1.0, tau_ref=1.0 + 7.5 * 0.125, seed=12)
+    f0 = O.init(O.Params(s=-1.0, **kw))
+    f0[2:] = random_state(N, 33, pi_amp=0.2, th_amp=0.3, e_amp=0.2)[2:]
+    cg = O.evolve(O.Params(s=-1.0, core_growth=True, **kw), f0.copy(), 0, n)
+    joined = O.evolve(O.Params(s=-1.0, **kw), f0.copy(), 0, k)
+    O.evolve(O.Params(s=1.0, **kw), joined, k, n - k)
+    assert np.array_equal(cg, joined)
+    only_s = O.evolve(O.Params(s=-1.0, **kw), f0.copy(), 0, n)
+    only_1 = O.evolve(O.Params(s=1.0, **kw), f0.copy(), 0, n)
+    assert np.max(np.abs(cg - only_s)) > 1e-4 and np.max(np.abs(cg - only_1)) > 1e-4
+    # s = 1 throughout is the true equations, whatever the switch time
+    a = O.evolve(O.Params(s=1.0, core_growth=True, **kw), f0.copy(), 0, n)
+    assert np.array_equal(a, only_1)

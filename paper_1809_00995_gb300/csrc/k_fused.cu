@@ -644,10 +644,12 @@ template <typename real, typename IT>
 cudaError_t launch_diag_it(const View<real> &v, int N, const DiagArgs &da, cudaStream_t st)
 {
     using G = Geo<real, 8, 1>;
-    if (G::smem > 48 * 1024) {
+    static bool configured = false;    // dynamic plus static (block reduction) may pass 48 KB
+    if (!configured) {
         const cudaError_t e = cudaFuncSetAttribute(k_fused_diag<real, IT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                    (int)G::smem);
         if (e != cudaSuccess) return e;
+        configured = true;
     }
     int tx, ty, nch, zc;
     fused_diag_grid(N, &tx, &ty, &nch, &zc);

@@ -70,6 +70,22 @@ def dist_env():
     return int(os.environ.get("RANK", 0)), int(os.environ.get("LOCAL_RANK", 0)), int(os.environ.get("WORLD_SIZE", 1))
 
 
+def max_over_ranks(dist, x, device):
+    """The largest of every rank's x (a replica job takes as long as its slowest
+    rank); x itself when there is no process group."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(world, n_sites, leapfrog_steps, seconds):
+    """Whole-job site-updates per second over all replicas."""
+    return world * n_sites * leapfrog_steps / seconds
+
+
 def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -365,12 +381,8 @@ def main():
     clocks = sampler.stop() if sampler else None
     t_ms = start.elapsed_time(end)
     step_ms = sum(x.elapsed_time(y) for x, y in ev)
-    t_max = t_ms
-    if dist:
-        tt = torch.tensor([t_ms], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_max = float(tt.item())
-    value = world * n_sites * diag_every * a.steps / (t_max / 1e3)
+    t_max = max_over_ranks(dist, t_ms, "cuda")
+    value = job_value(world, n_sites, diag_every * a.steps, t_max / 1e3)
 
     variant_name = info["variant_name"]
     g.close()
@@ -396,12 +408,8 @@ def main():
             obs_e2e = ah.ah_observables(h)
     finally:
         ah.ah_destroy(h)
-    t_e2e = time.perf_counter() - t0
-    if dist:
-        tt = torch.tensor([t_e2e], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_e2e = float(tt.item())
-    e2e_value = world * n_sites * diag_every * a.steps / t_e2e
+    t_e2e = max_over_ranks(dist, time.perf_counter() - t0, "cuda")
+    e2e_value = job_value(world, n_sites, diag_every * a.steps, t_e2e)
     d2h = ctypes.sizeof(ah.ah_obs)
     final_obs = obs_e2e
 

@@ -176,8 +176,8 @@ def cpu_oracle_rate(wl, budget_s=12.0, M=48):
     t_diag = time.perf_counter() - t1
     rate = M ** 3 / (t_step + t_diag / diag_every)
     cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
-    return rate, cores, "%d^3 window of the %d^3 workload, %d oracle steps (%.2f s/step) + 1 diagnostics pass " \
-                        "(%.2f s) weighted 1/%d" % (M, N, n, t_step, t_diag, diag_every)
+    return rate, cores, "%d^3 window of the %d^3 workload, %d oracle steps (%.2f ms/step) + 1 diagnostics pass " \
+                        "(%.1f ms) weighted 1/%d" % (M, N, n, 1e3 * t_step, 1e3 * t_diag, diag_every)
 
 
 def batch_configs(ah, count=64, seed=4):

@@ -35,6 +35,7 @@ namespace {
 
 constexpr int kZChunk = 64;        // planes per work item
 constexpr int kServerRound = 20;   // longest round of the server (admission latency bound)
+constexpr int kMaxBatchN = 1290;   // largest lattice side with 32-bit site indices (1290^3 < 2^31)
 
 double now_s()
 {
@@ -136,15 +137,17 @@ struct Engine {
         if (e == cudaSuccess) e = cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, dev);
         if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
         diag_blocks = diag_grid_blocks(num_sms);
+        // partials of the whole-lattice pass for the largest accepted lattice
+        const int nparts = std::max(diag_blocks, fused_diag_ctas(kMaxBatchN));
         list.capacity = 1 << 20;
-        if (e == cudaSuccess) e = cudaMalloc(&d_partials, sizeof(DiagPartial) * (diag_blocks + 1));
+        if (e == cudaSuccess) e = cudaMalloc(&d_partials, sizeof(DiagPartial) * (nparts + 1));
         if (e == cudaSuccess) e = cudaMalloc(&list.count, sizeof(unsigned long long) * (1 + list.capacity));
         if (e == cudaSuccess) e = cudaMallocHost(&h_result, sizeof(DiagPartial) + 64);
         if (e == cudaSuccess) e = cudaMalloc(&d_nitems, sizeof(int));
         if (e == cudaSuccess) e = cudaMalloc(&d_counter, sizeof(unsigned int));
         if (e == cudaSuccess) e = cudaMemsetAsync(d_counter, 0, sizeof(unsigned int), st);
         if (e != cudaSuccess) return e;
-        d_result = d_partials + diag_blocks;
+        d_result = d_partials + std::max(diag_blocks, fused_diag_ctas(kMaxBatchN));
         list.items = list.count + 1;
         h_count = reinterpret_cast<unsigned long long *>(h_result + 1);
         return cudaSuccess;
@@ -253,13 +256,14 @@ struct Engine {
         return cudaGraphLaunch(it->second, st);
     }
 
-    // Observables of one lattice at its current step (fast diagnostics, FP64 fallback).
+    // Observables of one lattice at its current step (the whole-lattice pass on
+    // the step's tile walk; everything in FP64 if the near-cut list overflows).
     ah_status diag(const Lat &L, ah_obs *out)
     {
         const View<float> v = lat_view(L);
         const Box b{ 0, 0, 0, L.N, L.N, L.N };
         const DiagCoef dc = host_diag_coef(L.cfg, L.step);
-        cudaError_t e = launch_diag<float>(v, L.N, b, dc, d_partials, diag_blocks, d_result, list, false, st);
+        cudaError_t e = launch_diag_whole<float>(v, L.N, dc, d_partials, d_result, list, diag_blocks, st);
         if (e == cudaSuccess) e = cudaMemcpyAsync(h_result, d_result, sizeof(DiagPartial), cudaMemcpyDeviceToHost, st);
         if (e == cudaSuccess)
             e = cudaMemcpyAsync(h_count, list.count, sizeof(unsigned long long), cudaMemcpyDeviceToHost, st);
@@ -294,7 +298,7 @@ ah_status check_batch_cfg(const ah_config &c)
 {
     if (c.precision != AH_FP32) return host_fail(AH_ERR_ARG, "batched lattices must be FP32 (precision AH_FP32)");
     if (c.diag_every < 0) return host_fail(AH_ERR_ARG, "diag_every must be >= 0");
-    if (c.N > 1290) return host_fail(AH_ERR_ARG, "batched lattices need N <= 1290 (32-bit site indices)");
+    if (c.N > kMaxBatchN) return host_fail(AH_ERR_ARG, "batched lattices need N <= 1290 (32-bit site indices)");
     return host_validate(c);
 }
 

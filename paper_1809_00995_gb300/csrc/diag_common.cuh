@@ -54,6 +54,13 @@ __device__ __forceinline__ bool unit_scale(C2<double> &z)
     z.i *= s;
     return true;
 }
+// unit_scale, or both parts NaN when z cannot be scaled (a plaquette with such
+// an edge is then left to the FP64 path by winding_scaled)
+template <typename T>
+__device__ __forceinline__ void unit_scale_or_nan(C2<T> &z)
+{
+    if (!unit_scale(z)) z.r = z.i = T(NAN);
+}
 // carry c of Arg u + Arg v = Arg(uv) + 2 pi c, Arg in (-pi, pi]
 template <typename T>
 __device__ __forceinline__ int carry(C2<T> u, C2<T> v, C2<T> uv)
@@ -71,6 +78,7 @@ __device__ __forceinline__ int winding_scaled(C2<T> z1, C2<T> z2, C2<T> z3, C2<T
 {
     const C2<T> w3 = conj(z3), w4 = conj(z4);
     const C2<T> q2 = cmul(z1, z2), q3 = cmul(q2, w3), q4 = cmul(q3, w4);
+    if (!(q4.r == q4.r)) return INT_MIN;            // an unscalable (NaN) edge
     if (near_cut(z1) | near_cut(z2) | near_cut(w3) | near_cut(w4) | near_cut(q4)) return INT_MIN;
     return carry(z1, z2, q2) + carry(q2, w3, q3) + carry(q3, w4, q4);
 }

@@ -72,7 +72,11 @@ struct Geo {
     static constexpr int PX = TX + 1, PY = TY + 1, NP = PX * PY;
     static constexpr int NPHALO = PX + TY;
     static constexpr size_t smem = sizeof(cpx<real>) * (2 * 3 * NE + 2 * NE) + sizeof(real) * 3 * NP;
-    static_assert(TY % 8 == 0 && NHALO <= NT && NPHALO <= NT, "tile shape");
+    // MODE_DIAG: the three scaled edge products of each site of plane z
+    // (tile, right column, top row) after the step's arrays
+    static constexpr size_t diag_off = (smem + 15) / 16 * 16;
+    static constexpr size_t smem_diag = diag_off + sizeof(cpx<real>) * 3 * NE;
+    static_assert(TY % 8 == 0 && NHALO <= NT && NPHALO <= NT && TX + TY <= NT, "tile shape");
 };
 
 // RX consecutive reals of one row (vector access when RX = 2; the pair never
@@ -112,6 +116,7 @@ __device__ __forceinline__ void fused_tile(const View<real> &v, int N, int zc, c
     cpx<real> *sU = reinterpret_cast<cpx<real> *>(smem_raw);   // [2 planes][3 dirs][NE]
     cpx<real> *sF = sU + 2 * 3 * NE;                            // [2 planes][NE] phi
     real *sP = reinterpret_cast<real *>(sF + 2 * NE);           // [3][NP] sin Xi_12, _13, _23
+    C2<real> *sE = reinterpret_cast<C2<real> *>(smem_raw + G::diag_off);   // MODE_DIAG: [3][NE] edges
 
     const int tid = threadIdx.x, lx = tid & 31, wy = tid >> 5;
     const int x0 = bx * TX, y0 = by * TY;
@@ -122,7 +127,7 @@ __device__ __forceinline__ void fused_tile(const View<real> &v, int N, int zc, c
     // (FP64), max |theta|, winding counters, non-finite sites
     Acc<real> dacc[14];
     real dtmax = real(0);
-    long long dic[kNumInt] = { 0, 0, 0, 0, 0, 0, 0, 0 };
+    int dic[kNumInt] = { 0, 0, 0, 0, 0, 0, 0, 0 };   // per thread at most 3 x 2048 planes x |W| <= 2
     // Gauss residual G = g_div div E + g_phi Im(conj(phi) Pi): FP64 for FP64
     // data; for FP32 data in double-float arithmetic (each G to about 2^-44 of
     // |g_div div E| + |g_phi Im(conj(phi) Pi)|), G^2 and that scale^2 summed
@@ -153,7 +158,10 @@ __device__ __forceinline__ void fused_tile(const View<real> &v, int N, int zc, c
             accd[15] = dgs2;
             double mx[kNumMax] = { dgmax, (double)dtmax };
             const int cta = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
-            block_reduce<256>(accd, mx, dic, &da->partials[cta]);
+            long long dil[kNumInt];
+#pragma unroll
+            for (int k = 0; k < kNumInt; ++k) dil[k] = dic[k];
+            block_reduce<256>(accd, mx, dil, &da->partials[cta]);
         }
     };
     if (z0 >= N) { diag_flush(); return; }
@@ -235,6 +243,16 @@ __device__ __forceinline__ void fused_tile(const View<real> &v, int N, int zc, c
     cpx<real> ph_m[NS], ph_0[NS], u3_m[NS];
     real th_0[NS][3], p13_m[NS], p23_m[NS];
     real e3_m[NS];                           // MODE_DIAG: E_3 of plane z-1
+    // MODE_DIAG: scaled edge products conj(phi^x) U_d^x phi^{x+d} of the own
+    // sites for d = 1, 2 in plane z (computed one plane ahead) and d = 3
+    using Z = C2<real>;
+    Z ed1[NS], ed2[NS], ed3[NS];
+    auto zc_ = [](cpx<real> a) { return Z{ a.r, a.i }; };
+    auto edge = [&](cpx<real> fa, cpx<real> u, cpx<real> fb) {
+        Z z = cmul(conj(zc_(fa)), cmul(zc_(u), zc_(fb)));
+        unit_scale_or_nan(z);
+        return z;
+    };
     if constexpr (DIAG) {
         const IT base = (IT)(z0 == 0 ? N - 1 : z0 - 1) * NN;
 #pragma unroll
@@ -264,6 +282,11 @@ __device__ __forceinline__ void fused_tile(const View<real> &v, int N, int zc, c
         u3_m[m] = Um[2 * NE + e];
         p13_m[m] = plaq(Um[e], Um[2 * NE + e + 1], U0[e], Um[2 * NE + e]);
         p23_m[m] = plaq(Um[NE + e], Um[2 * NE + e + EX], U0[NE + e], Um[2 * NE + e]);
+        if constexpr (DIAG) {
+            const cpx<real> *F0p = sF + b0 * NE;
+            ed1[m] = edge(F0p[e], U0[e], F0p[e + 1]);
+            ed2[m] = edge(F0p[e], U0[NE + e], F0p[e + EX]);
+        }
     }
     __syncthreads();
 
@@ -315,6 +338,28 @@ __device__ __forceinline__ void fused_tile(const View<real> &v, int N, int zc, c
             sP[G::NP + p] = p13[m];
             sP[2 * G::NP + p] = p23[m];
         }
+        if constexpr (DIAG) {
+            // own edges of plane z, then the right column's d = 2, 3 and the
+            // top row's d = 1, 3 edges that the tile's last column / row need
+            const cpx<real> *F0 = sF + bc * NE, *F1 = sF + bn * NE;
+#pragma unroll
+            for (int m = 0; m < NS; ++m) {
+                const int e = eix(m);
+                ed3[m] = edge(F0[e], U0[2 * NE + e], ph_p[m]);
+                sE[e] = ed1[m];
+                sE[NE + e] = ed2[m];
+                sE[2 * NE + e] = ed3[m];
+            }
+            if (tid < TY) {
+                const int e = (tid + 1) * EX + EX - 1;
+                sE[NE + e] = edge(F0[e], U0[NE + e], F0[e + EX]);
+                sE[2 * NE + e] = edge(F0[e], U0[2 * NE + e], F1[e]);
+            } else if (tid < TY + TX) {
+                const int e = (EY - 1) * EX + tid - TY + 1;
+                sE[e] = edge(F0[e], U0[e], F0[e + 1]);
+                sE[2 * NE + e] = edge(F0[e], U0[2 * NE + e], F1[e]);
+            }
+        }
         if (tid < G::NPHALO) {
             const int px = tid < PX ? tid : 0, py = tid < PX ? 0 : tid - PX + 1;
             const int e = py * EX + px, p = py * PX + px;
@@ -355,8 +400,13 @@ __device__ __forceinline__ void fused_tile(const View<real> &v, int N, int zc, c
             const real ne1 = c.c_edamp * e1[m] + c.c_cur * cu1 - c.c_curl * cl1;
             const real ne2 = c.c_edamp * e2[m] + c.c_cur * cu2 - c.c_curl * cl2;
             const real ne3 = c.c_edamp * e3[m] + c.c_cur * cu3 - c.c_curl * cl3;
-            if constexpr (DIAG) if (wr[m / RX]) {
+            Z ez1[NS], ez2[NS];              // MODE_DIAG: own d = 1, 2 edges of plane z+1
+            if constexpr (DIAG) {
                 const cpx<real> *F1 = sF + bn * NE;
+                ez1[m] = edge(F1[e], U1p[e], F1[e + 1]);
+                ez2[m] = edge(F1[e], U1p[NE + e], F1[e + EX]);
+            }
+            if constexpr (DIAG) if (wr[m / RX]) {
                 const real K = pr[m] * pr[m] + pim[m] * pim[m];
                 const real d1r = w1.r - f0.r, d1i = w1.i - f0.i, d2r = w2.r - f0.r, d2i = w2.i - f0.i;
                 const real d3r = w3.r - f0.r, d3i = w3.i - f0.i;
@@ -408,24 +458,13 @@ __device__ __forceinline__ void fused_tile(const View<real> &v, int N, int zc, c
                 }
                 // windings of the plaquettes (12), (13), (23) based at x (Eq. 9),
                 // edge products conj(phi^a) (U phi^b) as in k_diag_fast
-                using Z = C2<real>;
-                auto zc_ = [](cpx<real> a) { return Z{ a.r, a.i }; };
-                const Z f0c = conj(zc_(f0));
-                Z z1 = cmul(f0c, zc_(w1)), z2 = cmul(f0c, zc_(w2)), z3 = cmul(f0c, zc_(w3));
-                const Z fx = zc_(F0[e + 1]), fy = zc_(F0[e + EX]), fz = zc_(ph_p[m]);
-                Z z2_1 = cmul(conj(fx), cmul(zc_(U0[NE + e + 1]), zc_(F0[e + 1 + EX])));
-                Z z3_1 = cmul(conj(fx), cmul(zc_(U0[2 * NE + e + 1]), zc_(F1[e + 1])));
-                Z z1_2 = cmul(conj(fy), cmul(zc_(U0[e + EX]), zc_(F0[e + EX + 1])));
-                Z z3_2 = cmul(conj(fy), cmul(zc_(U0[2 * NE + e + EX]), zc_(F1[e + EX])));
-                Z z1_3 = cmul(conj(fz), cmul(zc_(U1p[e]), zc_(F1[e + 1])));
-                Z z2_3 = cmul(conj(fz), cmul(zc_(U1p[NE + e]), zc_(F1[e + EX])));
-                // each of the nine edge products scaled once (three are shared)
-                const bool k1 = unit_scale(z1), k2 = unit_scale(z2), k3 = unit_scale(z3);
-                const bool k21 = unit_scale(z2_1), k31 = unit_scale(z3_1), k12 = unit_scale(z1_2);
-                const bool k32 = unit_scale(z3_2), k13 = unit_scale(z1_3), k23 = unit_scale(z2_3);
-                const int wq[3] = { k1 & k21 & k12 & k2 ? winding_scaled(z1, z2_1, z1_2, z2) : INT_MIN,
-                                    k1 & k31 & k13 & k3 ? winding_scaled(z1, z3_1, z1_3, z3) : INT_MIN,
-                                    k2 & k32 & k23 & k3 ? winding_scaled(z2, z3_2, z2_3, z3) : INT_MIN };
+                // the twelve edges of the three plaquettes: own (this plane and,
+                // for d = 1, 2, the next), the x and y neighbours' from shared memory
+                const Z z2_1 = sE[NE + e + 1], z3_1 = sE[2 * NE + e + 1];
+                const Z z1_2 = sE[e + EX], z3_2 = sE[2 * NE + e + EX];
+                const int wq[3] = { winding_scaled(ed1[m], z2_1, z1_2, ed2[m]),
+                                    winding_scaled(ed1[m], z3_1, ez1[m], ed3[m]),
+                                    winding_scaled(ed2[m], z3_2, ez2[m], ed3[m]) };
                 const unsigned long long site =
                     (unsigned long long)((long long)z * N * (long long)N + (long long)roff[my] + mx);
 #pragma unroll
@@ -453,7 +492,11 @@ __device__ __forceinline__ void fused_tile(const View<real> &v, int N, int zc, c
                 o_t3[m] = wrap_phase(o_t3[m]);
             }
             // march: plane z becomes z-1
-            if constexpr (DIAG) e3_m[m] = e3[m];
+            if constexpr (DIAG) {
+                e3_m[m] = e3[m];
+                ed1[m] = ez1[m];
+                ed2[m] = ez2[m];
+            }
             ph_m[m] = f0;
             u3_m[m] = u3;
             p13_m[m] = q13;
@@ -647,13 +690,13 @@ cudaError_t launch_diag_it(const View<real> &v, int N, const DiagArgs &da, cudaS
     static bool configured = false;    // dynamic plus static (block reduction) may pass 48 KB
     if (!configured) {
         const cudaError_t e = cudaFuncSetAttribute(k_fused_diag<real, IT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                   (int)G::smem);
+                                                   (int)G::smem_diag);
         if (e != cudaSuccess) return e;
         configured = true;
     }
     int tx, ty, nch, zc;
     fused_diag_grid(N, &tx, &ty, &nch, &zc);
-    k_fused_diag<real, IT><<<dim3(tx, ty, nch), 256, G::smem, st>>>(v, N, zc, da);
+    k_fused_diag<real, IT><<<dim3(tx, ty, nch), 256, G::smem_diag, st>>>(v, N, zc, da);
     return cudaGetLastError();
 }
 }  // namespace

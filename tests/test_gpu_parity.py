@@ -355,3 +355,35 @@ def test_1024cubed_fp32_light_cone_windows():
         o = g.observables()
     assert o["n_sites"] == N ** 3 and o["nonfinite"] == 0
     assert o["gauss_rel"] < 1e-5
+
+
+def test_1300cubed_fp32_64bit_site_indices():
+    """The largest lattices (N^3 >= 2^31, up to the ~1660^3 FP32 state that fits
+    in HBM) take the 64-bit-index instantiations of the step and of the
+    diagnostics pass.  1300^3 FP32 (131 GB), radiation era: windows beyond linear
+    index 2^31 and across the seam equal the oracle after 20 steps, and the
+    whole-lattice diagnostics equal the site-parallel box kernel on the same
+    snapshot (sums to FP64 rounding of FP32 values, windings exactly)."""
+    N, k, b = 1300, 20, 12
+    assert N ** 3 >= 2 ** 31
+    p = oparams(N, ah.AH_RADIATION, 0.0, seed=6)
+    with sim(N, ah.AH_FP32, ah.AH_KERNEL_FUSED, ah.AH_RADIATION, 0.0, seed=6, flags=ah.AH_FLAG_AUTOTUNE) as g:
+        g.step(k)
+        for org in [(1295, 3, 1290), (640, 1297, 1280)]:
+            M = b + 2 * k
+            win = O.init(p, M=M, origin=[(o - k) % N for o in org])
+            win32 = win.astype(np.float32).astype(np.float64)
+            O.evolve(p, win32, 0, k)
+            got = g.fields(*org, b, b, b)
+            assert max(rel_err(got, win32[:, k:k + b, k:k + b, k:k + b])) <= TOL[ah.AH_FP32], org
+        whole = g.observables()
+        site = g.observables_box(1, 0, 0, N, N, N)      # the same sites, site-parallel kernel
+    assert whole["n_sites"] == N ** 3 and whole["nonfinite"] == 0 and whole["n_pierced"] > 0
+    assert whole["wind_abs_plane"] == site["wind_abs_plane"] and whole["wind_plane"] == site["wind_plane"]
+    assert whole["n_pierced"] == site["n_pierced"]
+    S1 = abs(site["sums"][1])
+    for kk in range(14):
+        scale = S1 if kk < 8 else S1 * S1 / N ** 3
+        assert abs(whole["sums"][kk] - site["sums"][kk]) <= 1e-6 * abs(site["sums"][kk]) + 1e-7 * scale, kk
+    assert whole["max_abs_theta"] == site["max_abs_theta"]
+    assert abs(whole["gauss_max"] - site["gauss_max"]) <= 1e-12 * max(1.0, site["gauss_max"])

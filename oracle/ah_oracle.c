@@ -22,7 +22,11 @@
  * Parity status: every function here is pinned by a CPU test (Philox
  * known-answer vectors, closed-form lattice waves, exact scalar recurrences,
  * Gauss-law conservation, gauge invariance, O(dt^2) energy conservation,
- * analytic string windings, light-cone locality); see tests/test_oracle_*.py.
+ * analytic string windings, light-cone locality, the compact-theta and
+ * core-growth identities); see tests/test_oracle_pins.py.  One part is parity
+ * unpinned: the mapping of two Philox output words to a uniform double in
+ * aho_site_uniform is a convention of this code (the paper draws its phases
+ * with cuRAND and gives no mapping), checked only for uniformity.
  */
 #include <math.h>
 #include <stdint.h>

@@ -86,6 +86,15 @@ struct DiagPartial {
 };
 
 struct Box { int x0, y0, z0, nx, ny, nz; };
+
+// Index (0..63) of the current device for per-device one-time set-up (kernel
+// attributes are set, and scratch is allocated, once on each device used).
+inline int device_slot()
+{
+    int d = 0;
+    cudaGetDevice(&d);
+    return d & 63;
+}
 struct DiagList;
 
 // Plaquettes whose winding the fast diagnostics leave to the FP64 path:

@@ -611,15 +611,16 @@ cudaError_t launch_shape(const View<real> &v, int N, const KickCoef<real> &c, in
     using G = Geo<real, TY, RX>;
     if (RX > 1 && (N & 1)) return cudaErrorInvalidValue;
     const bool idx32 = (long long)N * N * N < (1LL << 31);
-    static bool configured = false;   // once per instantiation
-    if (!configured) {
+    static unsigned long long configured = 0;   // per device, once per instantiation
+    const unsigned long long dev_bit = 1ULL << device_slot();
+    if (!(configured & dev_bit)) {
         cudaError_t e = cudaFuncSetAttribute(k_fused<real, TY, RX, MINB, int>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::smem);
         if (e == cudaSuccess)
             e = cudaFuncSetAttribute(k_fused<real, TY, RX, MINB, long long>,
                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::smem);
         if (e != cudaSuccess) return e;
-        configured = true;
+        configured |= dev_bit;
     }
     const int tx = (N + G::TX - 1) / G::TX, ty = (N + TY - 1) / TY;
     // enough z chunks for several waves of CTAs, chunks of at least min_chunk planes
@@ -687,12 +688,13 @@ template <typename real, typename IT>
 cudaError_t launch_diag_it(const View<real> &v, int N, const DiagArgs &da, cudaStream_t st)
 {
     using G = Geo<real, 8, 1>;
-    static bool configured = false;    // dynamic plus static (block reduction) may pass 48 KB
-    if (!configured) {
+    static unsigned long long configured = 0;   // per device; dynamic plus static smem may pass 48 KB
+    const unsigned long long dev_bit = 1ULL << device_slot();
+    if (!(configured & dev_bit)) {
         const cudaError_t e = cudaFuncSetAttribute(k_fused_diag<real, IT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                    (int)G::smem_diag);
         if (e != cudaSuccess) return e;
-        configured = true;
+        configured |= dev_bit;
     }
     int tx, ty, nch, zc;
     fused_diag_grid(N, &tx, &ty, &nch, &zc);
@@ -737,14 +739,16 @@ cudaError_t launch_batch_shape(const BatchLattice *lat, BatchState *state, int n
                                const int *nitems, unsigned int *counter, int num_sms, cudaStream_t st)
 {
     using G = Geo<float, TY, RX>;
-    static int blocks_per_sm = 0;
+    static int blocks_per_sm_dev[64] = {};      // per device
+    int &blocks_per_sm = blocks_per_sm_dev[device_slot()];
     if (!blocks_per_sm) {
         cudaError_t e = cudaFuncSetAttribute(k_fused_batch<TY, RX, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)G::smem);
         if (e != cudaSuccess) return e;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, k_fused_batch<TY, RX, MINB>, 256, G::smem);
+        int b = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_fused_batch<TY, RX, MINB>, 256, G::smem);
         if (e != cudaSuccess) return e;
-        if (blocks_per_sm < 1) blocks_per_sm = 1;
+        blocks_per_sm = b < 1 ? 1 : b;
     }
     k_fused_batch<TY, RX, MINB><<<num_sms * blocks_per_sm, 256, G::smem, st>>>(lat, state, items, nitems, counter);
     k_batch_advance<<<1, 256, 0, st>>>(lat, state, nlat, counter);
@@ -758,16 +762,28 @@ int batch_shape_count() { return (int)(sizeof(kBatchShapes) / sizeof(kBatchShape
 // any stream capture: a launch of an empty work list.
 cudaError_t batch_shape_prepare(int shape, int num_sms, cudaStream_t st)
 {
-    static BatchState *d_dummy = nullptr;
-    static int *d_zero = nullptr;
-    static unsigned int *d_cnt = nullptr;
+    // a few bytes of device scratch per device, kept for the life of the process
+    static BatchState *d_dummy_dev[64] = {};
+    static int *d_zero_dev[64] = {};
+    static unsigned int *d_cnt_dev[64] = {};
+    const int ds = device_slot();
+    BatchState *&d_dummy = d_dummy_dev[ds];
+    int *&d_zero = d_zero_dev[ds];
+    unsigned int *&d_cnt = d_cnt_dev[ds];
     if (!d_dummy) {
-        cudaError_t e = cudaMalloc(&d_dummy, sizeof(BatchState));
-        if (e == cudaSuccess) e = cudaMalloc(&d_zero, sizeof(int));
-        if (e == cudaSuccess) e = cudaMalloc(&d_cnt, sizeof(unsigned int));
-        if (e == cudaSuccess) e = cudaMemsetAsync(d_zero, 0, sizeof(int), st);
-        if (e == cudaSuccess) e = cudaMemsetAsync(d_cnt, 0, sizeof(unsigned int), st);
-        if (e != cudaSuccess) return e;
+        BatchState *a = nullptr;
+        int *z = nullptr;
+        unsigned int *c = nullptr;
+        cudaError_t e = cudaMalloc(&a, sizeof(BatchState));
+        if (e == cudaSuccess) e = cudaMalloc(&z, sizeof(int));
+        if (e == cudaSuccess) e = cudaMalloc(&c, sizeof(unsigned int));
+        if (e == cudaSuccess) e = cudaMemsetAsync(z, 0, sizeof(int), st);
+        if (e == cudaSuccess) e = cudaMemsetAsync(c, 0, sizeof(unsigned int), st);
+        if (e != cudaSuccess) {
+            cudaFree(a); cudaFree(z); cudaFree(c);
+            return e;
+        }
+        d_dummy = a; d_zero = z; d_cnt = c;
     }
     // nlat = 0: the advance kernel touches no lattice; nitems = 0: no work
     return launch_fused_batch(shape, nullptr, d_dummy, 0, nullptr, d_zero, d_cnt, num_sms, st);

@@ -285,12 +285,13 @@ template <int TY, int MINB>
 cudaError_t launch_pair_shape(const View<float> &v, int N, const KickCoef<float> &c, int min_chunk, cudaStream_t st)
 {
     using G = PGeo<TY>;
-    static bool configured = false;
-    if (!configured) {
+    static unsigned long long configured = 0;   // per device
+    const unsigned long long dev_bit = 1ULL << device_slot();
+    if (!(configured & dev_bit)) {
         cudaError_t e = cudaFuncSetAttribute(k_pair<TY, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)G::smem);
         if (e != cudaSuccess) return e;
-        configured = true;
+        configured |= dev_bit;
     }
     const int tx = (N + OWNW - 1) / OWNW, ty = (N + TY - 1) / TY;
     int nch = (int)((152LL * 16 + (long long)tx * ty - 1) / ((long long)tx * ty));

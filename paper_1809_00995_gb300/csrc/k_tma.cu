@@ -323,12 +323,13 @@ template <int MINB>
 cudaError_t launch_minb(const TmaMaps &maps, const View<float> &v, int N, const KickCoef<float> &c, int *err,
                         int min_chunk, cudaStream_t st)
 {
-    static bool configured = false;
-    if (!configured) {
+    static unsigned long long configured = 0;   // per device
+    const unsigned long long dev_bit = 1ULL << device_slot();
+    if (!(configured & dev_bit)) {
         cudaError_t e = cudaFuncSetAttribute(k_fused_tma<MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)(sizeof(Smem) + 128));
         if (e != cudaSuccess) return e;
-        configured = true;
+        configured |= dev_bit;
     }
     const int tx = N / TX, ty = N / TY;
     int nch = (int)((152LL * 3 * 4 + (long long)tx * ty - 1) / ((long long)tx * ty));

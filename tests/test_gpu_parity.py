@@ -387,3 +387,23 @@ def test_1300cubed_fp32_64bit_site_indices():
         assert abs(whole["sums"][kk] - site["sums"][kk]) <= 1e-6 * abs(site["sums"][kk]) + 1e-7 * scale, kk
     assert whole["max_abs_theta"] == site["max_abs_theta"]
     assert abs(whole["gauss_max"] - site["gauss_max"]) <= 1e-12 * max(1.0, site["gauss_max"])
+
+
+@pytest.mark.parametrize("precision", [ah.AH_FP64, ah.AH_FP32])
+def test_zero_gradient_denominators_are_reported_not_trapped(precision):
+    """Uniform phi with Pi != 0: |D phi|^2 = 0 at every site, so R_V = sum K V /
+    sum G2 V divides by zero; the observables carry IEEE inf/NaN for the velocity
+    estimators (as the oracle does) and the call still succeeds."""
+    N = 8
+    f = np.zeros((10, N, N, N))
+    f[0], f[1] = 0.6, 0.5                     # uniform phi, |phi|^2 != sigma^2 so V != 0
+    f[2], f[3] = 0.3, -0.1                    # uniform Pi
+    p = oparams(N, ah.AH_MINKOWSKI)
+    with sim(N, precision, ah.AH_KERNEL_FUSED, ah.AH_MINKOWSKI) as g:
+        g.set_fields(f, step=0)
+        go = g.observables()
+    oo = O.observables(p, f, 0)
+    assert go["sums"][4] == 0.0 and go["sums"][9] == 0.0          # sum G2, sum G2 V
+    assert math.isinf(go["R_V"]) and math.isinf(oo["R_V"])
+    assert math.isnan(go["v2_V"]) and math.isnan(oo["v2_V"])
+    assert go["nonfinite"] == 0

@@ -451,6 +451,7 @@ ah_status ah_create_ex(const ah_config *cfg, ah_sim **out)
     h->cfg = *cfg;
     if (h->cfg.kernel == AH_KERNEL_AUTO) h->cfg.kernel = AH_KERNEL_FUSED;
     h->N = cfg->N;
+    h->variant = cfg->precision == AH_FP32 ? fused_default_variant<float>() : fused_default_variant<double>();
     h->nsites = (long long)cfg->N * cfg->N * cfg->N;
     h->step = 0;
     h->cur = 0;

@@ -132,6 +132,8 @@ template <typename real>
 const char *fused_variant_name(int variant);
 template <typename real>
 bool fused_variant_ok(int variant, int N);
+template <typename real>
+int fused_default_variant();
 
 template <typename real>
 cudaError_t launch_diag(const View<real> &v, int N, Box b, const DiagCoef &c,

@@ -594,19 +594,57 @@ __global__ void k_batch_advance(const BatchLattice *lat, BatchState *state, int 
 // Compile-time shapes of the fused step: tile height TY (TY/8 rows per thread),
 // RX sites per thread in x (tile width 32 RX; RX = 2 uses 8-byte vector
 // accesses and needs an even N), and the minimum resident CTAs per SM the
-// register allocation must allow; min_chunk is the shortest z chunk.
-struct VariantInfo { int ty, rx, minb, min_chunk; const char *name; };
+// register allocation must allow; min_chunk is the shortest z chunk.  The z
+// chunk count is either "about 16 waves of CTAs" or (_w) the wave-quantisation
+// model of choose_chunks.
+struct VariantInfo { int ty, rx, minb, min_chunk; bool wave_model; const char *name; };
 constexpr VariantInfo kVariants32[] = {
-    { 16, 1, 2, 16, "ty16_b2" }, { 16, 1, 3, 16, "ty16_b3" }, { 8, 1, 4, 16, "ty8_b4" },
-    { 8, 1, 3, 16, "ty8_b3" },  { 32, 1, 1, 16, "ty32_b1" }, { 16, 1, 2, 64, "ty16_b2_z64" },
-    { 8, 2, 3, 16, "x2_ty8_b3" }, { 8, 2, 2, 16, "x2_ty8_b2" }, { 16, 2, 2, 16, "x2_ty16_b2" },
-    { 16, 2, 1, 16, "x2_ty16_b1" },
+    { 16, 1, 2, 16, false, "ty16_b2" }, { 16, 1, 3, 16, false, "ty16_b3" }, { 8, 1, 4, 16, false, "ty8_b4" },
+    { 8, 1, 3, 16, false, "ty8_b3" },  { 32, 1, 1, 16, false, "ty32_b1" }, { 16, 1, 2, 64, false, "ty16_b2_z64" },
+    { 8, 2, 3, 16, false, "x2_ty8_b3" }, { 8, 2, 2, 16, false, "x2_ty8_b2" }, { 16, 2, 2, 16, false, "x2_ty16_b2" },
+    { 16, 2, 1, 16, false, "x2_ty16_b1" }, { 8, 1, 4, 16, true, "ty8_b4_w" }, { 8, 1, 3, 16, true, "ty8_b3_w" },
+    { 8, 2, 2, 16, true, "x2_ty8_b2_w" }, { 16, 1, 2, 16, true, "ty16_b2_w" },
 };
-constexpr VariantInfo kVariants64[] = { { 16, 1, 1, 16, "ty16_b1" }, { 8, 1, 2, 16, "ty8_b2" },
-                                        { 8, 2, 1, 16, "x2_ty8_b1" } };
+constexpr VariantInfo kVariants64[] = { { 16, 1, 1, 16, false, "ty16_b1" }, { 8, 1, 2, 16, false, "ty8_b2" },
+                                        { 8, 2, 1, 16, false, "x2_ty8_b1" }, { 8, 1, 2, 16, true, "ty8_b2_w" } };
+
+// Number of z chunks for `tiles` XY tiles of an N-plane lattice when `slots`
+// CTAs are resident at once: the grid runs in waves of `slots` CTAs, each CTA
+// marching its chunk plus two extra planes (the one below, read in the
+// prologue, and the prefetch past the top), so minimise
+// ceil(tiles n / slots) (ceil(N / n) + 2) over n with chunks of at least
+// min_chunk planes.
+int choose_chunks(int N, long long tiles, int slots, int min_chunk)
+{
+    const int nmax = std::max(1, std::min(N / std::max(1, min_chunk), 64));
+    int best = 1;
+    long long best_cost = -1;
+    for (int n = 1; n <= nmax; ++n) {
+        const long long waves = (tiles * n + slots - 1) / slots;
+        const long long cost = waves * ((N + n - 1) / n + 2);
+        if (best_cost < 0 || cost < best_cost) {
+            best_cost = cost;
+            best = n;
+        }
+    }
+    return best;
+}
+
+int device_sm_count()
+{
+    static int sms[64] = {};
+    int &n = sms[device_slot()];
+    if (!n) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n < 1) n = 152;
+    }
+    return n;
+}
 
 template <typename real, int TY, int RX, int MINB>
-cudaError_t launch_shape(const View<real> &v, int N, const KickCoef<real> &c, int min_chunk, cudaStream_t st)
+cudaError_t launch_shape(const View<real> &v, int N, const KickCoef<real> &c, int min_chunk, bool wave_model,
+                         cudaStream_t st)
 {
     using G = Geo<real, TY, RX>;
     if (RX > 1 && (N & 1)) return cudaErrorInvalidValue;
@@ -623,9 +661,14 @@ cudaError_t launch_shape(const View<real> &v, int N, const KickCoef<real> &c, in
         configured |= dev_bit;
     }
     const int tx = (N + G::TX - 1) / G::TX, ty = (N + TY - 1) / TY;
-    // enough z chunks for several waves of CTAs, chunks of at least min_chunk planes
-    int nch = (int)((152LL * 16 + (long long)tx * ty - 1) / ((long long)tx * ty));
-    nch = max(1, min(nch, N / min_chunk));
+    int nch;
+    if (wave_model) {
+        nch = choose_chunks(N, (long long)tx * ty, device_sm_count() * MINB, min_chunk);
+    } else {
+        // enough z chunks for several waves of CTAs, chunks of at least min_chunk planes
+        nch = (int)((16LL * device_sm_count() + (long long)tx * ty - 1) / ((long long)tx * ty));
+        nch = max(1, min(nch, N / min_chunk));
+    }
     const int zc = (N + nch - 1) / nch;
     nch = (N + zc - 1) / zc;
     if (idx32) k_fused<real, TY, RX, MINB, int><<<dim3(tx, ty, nch), G::NT, G::smem, st>>>(v, N, zc, c);
@@ -634,6 +677,13 @@ cudaError_t launch_shape(const View<real> &v, int N, const KickCoef<real> &c, in
 }
 
 }  // namespace
+
+// Shape used when a simulation is not autotuned: the fastest on GB300 at
+// 512^3 and 1024^3 (any N; RX = 1).
+template <>
+int fused_default_variant<float>() { return 10; }      // ty8_b4_w
+template <>
+int fused_default_variant<double>() { return 1; }      // ty8_b2
 
 template <>
 int fused_variant_count<float>() { return (int)(sizeof(kVariants32) / sizeof(kVariants32[0])); }
@@ -653,18 +703,24 @@ template <>
 cudaError_t launch_fused_step<float>(const View<float> &v, int N, const KickCoef<float> &c, int variant,
                                      cudaStream_t st)
 {
+    if (variant < 0 || variant >= fused_variant_count<float>()) return cudaErrorInvalidValue;
     const int mc = kVariants32[variant].min_chunk;
+    const bool wm = kVariants32[variant].wave_model;
     switch (variant) {
-    case 0: return launch_shape<float, 16, 1, 2>(v, N, c, mc, st);
-    case 1: return launch_shape<float, 16, 1, 3>(v, N, c, mc, st);
-    case 2: return launch_shape<float, 8, 1, 4>(v, N, c, mc, st);
-    case 3: return launch_shape<float, 8, 1, 3>(v, N, c, mc, st);
-    case 4: return launch_shape<float, 32, 1, 1>(v, N, c, mc, st);
-    case 5: return launch_shape<float, 16, 1, 2>(v, N, c, mc, st);
-    case 6: return launch_shape<float, 8, 2, 3>(v, N, c, mc, st);
-    case 7: return launch_shape<float, 8, 2, 2>(v, N, c, mc, st);
-    case 8: return launch_shape<float, 16, 2, 2>(v, N, c, mc, st);
-    case 9: return launch_shape<float, 16, 2, 1>(v, N, c, mc, st);
+    case 0: return launch_shape<float, 16, 1, 2>(v, N, c, mc, wm, st);
+    case 1: return launch_shape<float, 16, 1, 3>(v, N, c, mc, wm, st);
+    case 2: return launch_shape<float, 8, 1, 4>(v, N, c, mc, wm, st);
+    case 3: return launch_shape<float, 8, 1, 3>(v, N, c, mc, wm, st);
+    case 4: return launch_shape<float, 32, 1, 1>(v, N, c, mc, wm, st);
+    case 5: return launch_shape<float, 16, 1, 2>(v, N, c, mc, wm, st);
+    case 6: return launch_shape<float, 8, 2, 3>(v, N, c, mc, wm, st);
+    case 7: return launch_shape<float, 8, 2, 2>(v, N, c, mc, wm, st);
+    case 8: return launch_shape<float, 16, 2, 2>(v, N, c, mc, wm, st);
+    case 9: return launch_shape<float, 16, 2, 1>(v, N, c, mc, wm, st);
+    case 10: return launch_shape<float, 8, 1, 4>(v, N, c, mc, wm, st);
+    case 11: return launch_shape<float, 8, 1, 3>(v, N, c, mc, wm, st);
+    case 12: return launch_shape<float, 8, 2, 2>(v, N, c, mc, wm, st);
+    case 13: return launch_shape<float, 16, 1, 2>(v, N, c, mc, wm, st);
     default: return cudaErrorInvalidValue;
     }
 }
@@ -672,11 +728,14 @@ template <>
 cudaError_t launch_fused_step<double>(const View<double> &v, int N, const KickCoef<double> &c, int variant,
                                       cudaStream_t st)
 {
+    if (variant < 0 || variant >= fused_variant_count<double>()) return cudaErrorInvalidValue;
     const int mc = kVariants64[variant].min_chunk;
+    const bool wm = kVariants64[variant].wave_model;
     switch (variant) {
-    case 0: return launch_shape<double, 16, 1, 1>(v, N, c, mc, st);
-    case 1: return launch_shape<double, 8, 1, 2>(v, N, c, mc, st);
-    case 2: return launch_shape<double, 8, 2, 1>(v, N, c, mc, st);
+    case 0: return launch_shape<double, 16, 1, 1>(v, N, c, mc, wm, st);
+    case 1: return launch_shape<double, 8, 1, 2>(v, N, c, mc, wm, st);
+    case 2: return launch_shape<double, 8, 2, 1>(v, N, c, mc, wm, st);
+    case 3: return launch_shape<double, 8, 1, 2>(v, N, c, mc, wm, st);
     default: return cudaErrorInvalidValue;
     }
 }

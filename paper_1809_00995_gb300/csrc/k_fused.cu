@@ -766,8 +766,7 @@ void fused_diag_grid(int N, int *tx, int *ty, int *nch, int *zc)
 {
     *tx = (N + 31) / 32;
     *ty = (N + 7) / 8;
-    int n = (int)((152LL * 16 + (long long)*tx * *ty - 1) / ((long long)*tx * *ty));
-    n = max(1, min(n, N / 16));
+    const int n = choose_chunks(N, (long long)*tx * *ty, 2 * device_sm_count(), 16);   // 2 CTAs / SM
     *zc = (N + n - 1) / n;
     *nch = (N + *zc - 1) / *zc;
 }

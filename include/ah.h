@@ -154,10 +154,11 @@ ah_sim *ah_create(int32_t N, double dx, double dt, int32_t era, double s,
                   double lambda0, double e0, uint64_t seed);
 
 /* Create from a full configuration.  Validates the arguments (AH_ERR_ARG),
- * rejects a stiff scalar mode that breaks leapfrog stability,
- * sqrt(lambda0) sigma max_tau a(tau)^s dt >= 1, with AH_ERR_UNSTABLE, allocates
- * the state on the current CUDA device (AH_ERR_OOM) and writes the initial
- * state.  *out receives the handle. */
+ * rejects with AH_ERR_UNSTABLE a configuration whose stiffest mode breaks
+ * leapfrog stability, dt^2 (12/dx^2 + max(lambda0, 2 e0^2) sigma^2 a^(2s)) >= 3.6
+ * for the largest a^(2s) over the run (over both stretches of a core-growth
+ * schedule), allocates the state on the current CUDA device (AH_ERR_OOM) and
+ * writes the initial state.  *out receives the handle. */
 ah_status ah_create_ex(const ah_config *cfg, ah_sim **out);
 
 /* Enqueue nsteps leapfrog steps (Eqs. up_pi, up_E, up_phi, up_A) on the
@@ -165,9 +166,13 @@ ah_status ah_create_ex(const ah_config *cfg, ah_sim **out);
 ah_status ah_step(ah_sim *sim, int64_t nsteps);
 
 /* Compute the observables of the current state over the whole lattice and
- * write them to *out (waits for the simulation's stream).  The per-site
- * values and all sums are FP64 whatever the state precision.  Returns
- * AH_ERR_NONFINITE (with *out filled) if any site is not finite. */
+ * write them to *out (waits for the simulation's stream).  Per-site energies
+ * are evaluated in the state precision and summed with compensation per thread
+ * and in FP64 across threads; the Gauss residual in FP64 (double-float
+ * arithmetic for an FP32 state); windings equal the FP64 arctangent formula of
+ * Eq. 9 on the same snapshot.  With AH_FLAG_EXACT_DIAG everything per site is
+ * FP64.  Returns AH_ERR_NONFINITE (with *out filled) if any site is not
+ * finite. */
 ah_status ah_observables(ah_sim *sim, ah_obs *out);
 
 /* Same over the sub-box [x0, x0+nx) x [y0, y0+ny) x [z0, z0+nz), taken mod N
@@ -211,8 +216,9 @@ typedef struct ah_info {
 } ah_info;
 ah_status ah_get_info(const ah_sim *sim, ah_info *out);
 
-/* Number of compile-time shapes (tile height, resident CTAs per SM, z-chunk
- * length) of the fused step for the given precision. */
+/* Number of shapes of the fused step for the given precision (tile size,
+ * resident CTAs per SM, z-chunk rule; for FP32 also the paired-FP32 and the
+ * TMA-fed kernels).  The names are in ah_info.variant_name. */
 int32_t ah_variant_count(int32_t precision);
 
 /* Select the fused-step shape for later steps (0 <= variant < count).  Every
@@ -225,7 +231,7 @@ ah_status ah_set_variant(ah_sim *sim, int32_t variant);
  * (AH_ERR_BUSY otherwise).  Waits for the simulation's stream. */
 ah_status ah_autotune(ah_sim *sim, int32_t trial_steps, int32_t *chosen);
 
-/* ---- batched ensembles (the ensembles of independent runs of Sec. 4) ----
+/* ---- batched ensembles (the ensembles of independent runs of Sec. 4, Table 3) ----
  *
  * Many independent FP32 lattices (any mix of N, era, s, seed) advance together:
  * one persistent kernel launch per leapfrog step covers every resident lattice

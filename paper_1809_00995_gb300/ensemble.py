@@ -1,4 +1,4 @@
-"""Scaling ensembles of string networks (Sec. 3 of arXiv:1809.00995, Table 3).
+"""Scaling ensembles of string networks (Sec. 4 of arXiv:1809.00995, Table 3).
 
 A case (era, s, schedule) is run for several seeds as one batched job through
 ah_batch_run; each run's diagnostic series gives

@@ -103,3 +103,23 @@ def test_wrapping_keeps_fp32_resolution_at_large_theta():
     # every step: theta and the fields it drives are several times closer
     assert max(eb[4:7]) * 3 < max(ea[4:7]), (ea, eb)
     assert max(eb) * 2 < max(ea), (ea, eb)
+
+
+def test_batched_path_wraps_theta():
+    """A batched lattice with AH_FLAG_WRAP_THETA gives the single-lattice run's
+    observables (same flag) within the FP32 diagnostic tolerance, with every
+    phase in [-pi, pi] (max |theta| reported by the final diagnostics)."""
+    kw = dict(era=ah.AH_MINKOWSKI, seed=7, flags=ah.AH_FLAG_WRAP_THETA, diag_every=0, tau_end=31.0)
+    cfgs = [ah.config(24, **kw), ah.config(16, **kw)]
+    series, _ = ah.ah_batch_run(cfgs)
+    for cfg, ser in zip(cfgs, series):
+        with ah.Sim(cfg.N, era=ah.AH_MINKOWSKI, seed=7, flags=ah.AH_FLAG_WRAP_THETA, tau_end=31.0,
+                    kernel=ah.AH_KERNEL_FUSED) as g:
+            g.step(int(round((cfg.tau_end - cfg.tau0) / cfg.dt)))
+            ref = g.observables()
+        got = ser[-1]
+        assert got["step"] == ref["step"] == 300
+        scale = abs(ref["sums"][1])
+        for k in range(8):
+            assert abs(got["sums"][k] - ref["sums"][k]) <= 2e-5 * scale, k
+        assert got["max_abs_theta"] <= np.pi * (1 + 1e-6) and ref["max_abs_theta"] <= np.pi * (1 + 1e-6)

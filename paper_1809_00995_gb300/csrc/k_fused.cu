@@ -18,6 +18,15 @@
 // Pi and E are updated in place, so every step reads and writes the 10-real
 // state exactly once from DRAM; halo re-reads are served by L2.  Periodic
 // boundaries are applied in the index arithmetic.
+//
+// The same tile walk serves three kernels: k_fused (one lattice, one step),
+// k_fused_batch (persistent CTAs over the tiles of many lattices) and, in
+// MODE_DIAG, k_fused_diag (the whole-lattice diagnostics of Sec. 2: energy
+// sums, Gauss residual and plaquette windings of the current state, nothing
+// written back).  The shapes (tile height, sites per thread in x, resident
+// CTAs per SM) and the number of z chunks per column are chosen by the
+// autotuner; a chunk count that fills the last wave of CTAs matters because
+// each CTA marches a whole chunk.
 #include "ah_internal.cuh"
 #include "diag_common.cuh"
 #include "sincos32.cuh"

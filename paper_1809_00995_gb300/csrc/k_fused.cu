@@ -465,10 +465,10 @@ __device__ __forceinline__ void fused_tile(const View<real> &v, int N, int zc, c
                         if (Gs.h > fgmax.h || (Gs.h == fgmax.h && Gs.l > fgmax.l)) fgmax = Gs;
                     }
                 }
-                // windings of the plaquettes (12), (13), (23) based at x (Eq. 9),
-                // edge products conj(phi^a) (U phi^b) as in k_diag_fast
-                // the twelve edges of the three plaquettes: own (this plane and,
-                // for d = 1, 2, the next), the x and y neighbours' from shared memory
+                // windings of the plaquettes (12), (13), (23) based at x (Eq. 9)
+                // from their twelve edge products conj(phi^a) U phi^b: the own
+                // ones (this plane and, for d = 1, 2, the next) and the x and y
+                // neighbours' from shared memory
                 const Z z2_1 = sE[NE + e + 1], z3_1 = sE[2 * NE + e + 1];
                 const Z z1_2 = sE[e + EX], z3_2 = sE[2 * NE + e + EX];
                 const int wq[3] = { winding_scaled(ed1[m], z2_1, z1_2, ed2[m]),

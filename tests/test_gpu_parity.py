@@ -407,3 +407,19 @@ def test_zero_gradient_denominators_are_reported_not_trapped(precision):
     assert math.isinf(go["R_V"]) and math.isinf(oo["R_V"])
     assert math.isnan(go["v2_V"]) and math.isnan(oo["v2_V"])
     assert go["nonfinite"] == 0
+
+
+@pytest.mark.parametrize("precision", [ah.AH_FP64, ah.AH_FP32])
+@pytest.mark.parametrize("N", [4, 5, 7])
+def test_observables_on_the_smallest_lattices(N, precision):
+    """Lattices smaller than one 32 x 8 tile (the tile wraps onto itself, every
+    neighbour is a periodic image): whole-lattice diagnostics equal the oracle's
+    on the same snapshot, windings exactly."""
+    p = oparams(N, ah.AH_RADIATION, 0.0, seed=N)
+    f = random_state(N, 50 + N, th_amp=2.0, phi_amp=1.0)
+    with sim(N, precision, ah.AH_KERNEL_FUSED, ah.AH_RADIATION, 0.0, seed=N) as g:
+        g.set_fields(f, step=5)
+        g.step(3)
+        snap = g.fields()
+        go = g.observables()
+    compare_obs(go, O.observables(p, snap, 8), precision)

@@ -19,6 +19,7 @@
 
 #include "../../include/ah.h"
 #include "ah_internal.cuh"
+#include "trace.h"
 
 using namespace ah;
 
@@ -442,6 +443,7 @@ void ah_config_default(ah_config *c, int32_t N)
 
 ah_status ah_create_ex(const ah_config *cfg, ah_sim **out)
 {
+    TraceRange tr("ah_create");
     if (!cfg || !out) return fail(AH_ERR_ARG, "null argument");
     *out = nullptr;
     ah_status st = validate(*cfg);
@@ -539,6 +541,7 @@ ah_sim *ah_create(int32_t N, double dx, double dt, int32_t era, double s, double
 
 ah_status ah_step(ah_sim *h, int64_t nsteps)
 {
+    TraceRange tr("ah_step");
     ah_status st = enter(h);
     if (st != AH_OK) return st;
     if (nsteps < 0) return fail(AH_ERR_ARG, "nsteps must be >= 0");
@@ -554,6 +557,7 @@ ah_status ah_step(ah_sim *h, int64_t nsteps)
 ah_status ah_observables_box(ah_sim *h, int32_t x0, int32_t y0, int32_t z0, int32_t nx, int32_t ny,
                              int32_t nz, ah_obs *out)
 {
+    TraceRange tr("ah_observables");
     ah_status st = enter(h);
     if (st != AH_OK) return st;
     if (!out) return fail(AH_ERR_ARG, "null output");
@@ -678,6 +682,7 @@ ah_status ah_set_variant(ah_sim *h, int32_t variant)
 
 ah_status ah_autotune(ah_sim *h, int32_t trial_steps, int32_t *chosen)
 {
+    TraceRange tr("ah_autotune");
     ah_status st = enter(h);
     if (st != AH_OK) return st;
     if (!h->pristine) return fail(AH_ERR_BUSY, "autotune needs the freshly created state");

@@ -28,6 +28,7 @@
 
 #include "../../include/ah.h"
 #include "ah_internal.cuh"
+#include "trace.h"
 
 using namespace ah;
 
@@ -226,6 +227,7 @@ struct Engine {
     // R batched steps of every loaded lattice (graph replay when enabled).
     cudaError_t steps(int R)
     {
+        TraceRange tr("batch steps");
         if (R <= 0) return cudaSuccess;
         launches += 2LL * R;
         ++rounds;
@@ -260,6 +262,7 @@ struct Engine {
     // the step's tile walk; everything in FP64 if the near-cut list overflows).
     ah_status diag(const Lat &L, ah_obs *out)
     {
+        TraceRange tr("batch diagnostics");
         const View<float> v = lat_view(L);
         const Box b{ 0, 0, 0, L.N, L.N, L.N };
         const DiagCoef dc = host_diag_coef(L.cfg, L.step);

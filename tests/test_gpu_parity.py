@@ -423,3 +423,14 @@ def test_observables_on_the_smallest_lattices(N, precision):
         snap = g.fields()
         go = g.observables()
     compare_obs(go, O.observables(p, snap, 8), precision)
+
+
+def test_state_larger_than_hbm_reports_oom_and_the_device_stays_usable():
+    """2048^3 FP32 needs 515 GB of state: creation fails with AH_ERR_OOM (a refused
+    allocation, no fault) and the next simulation on the device works."""
+    with pytest.raises(ah.AhError) as e:
+        ah.ah_create_ex(ah.config(2048))
+    assert e.value.status == ah.AH_ERR_OOM
+    with sim(16, ah.AH_FP32, ah.AH_KERNEL_FUSED) as g:
+        g.step(3)
+        assert g.observables()["nonfinite"] == 0

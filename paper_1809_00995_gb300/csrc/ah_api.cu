@@ -477,8 +477,10 @@ ah_status ah_create_ex(const ah_config *cfg, ah_sim **out)
         e = cudaMalloc((void **)&h->list.count, sizeof(unsigned long long) * (1 + h->list.capacity));
     if (e == cudaSuccess) e = cudaMallocHost((void **)&h->host_result, sizeof(DiagPartial) + 32);
     if (e != cudaSuccess) {
+        const double gb = h->dbytes / 1e9;
+        cudaGetLastError();                  // a refused allocation is not a sticky error: clear it
         ah_destroy(h);
-        return fail(AH_ERR_OOM, "allocation of %.3g GB failed: %s", h->dbytes / 1e9, cudaGetErrorString(e));
+        return fail(AH_ERR_OOM, "allocation of %.3g GB failed: %s", gb, cudaGetErrorString(e));
     }
     h->result = h->partials + nparts;
     h->list.items = h->list.count + 1;

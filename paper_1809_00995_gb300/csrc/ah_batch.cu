@@ -77,7 +77,11 @@ cudaError_t lat_setup(Lat &L, cudaStream_t st)
     L.cur = 0;
     L.bytes = lattice_bytes(L.cfg);
     cudaError_t e = cudaMallocAsync(&L.mem, L.bytes, st);
-    if (e != cudaSuccess) { L.mem = nullptr; return e; }
+    if (e != cudaSuccess) {
+        L.mem = nullptr;
+        cudaGetLastError();                  // clear the refused allocation's error
+        return e;
+    }
     host_carve32(L.F, L.mem, (size_t)L.nsites);
     L.coefs = reinterpret_cast<KickCoef<float> *>(static_cast<char *>(L.mem) + align256(host_state_bytes32(L.nsites)));
     std::vector<KickCoef<float>> tab(std::max(1, L.nsteps));

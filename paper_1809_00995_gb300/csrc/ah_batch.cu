@@ -16,6 +16,7 @@
 #include <algorithm>
 #include <chrono>
 #include <condition_variable>
+#include <cstdlib>
 #include <cstring>
 #include <deque>
 #include <map>
@@ -448,6 +449,11 @@ struct ah_server {
     Engine eng;
     std::thread worker;
     int device = 0;
+    // host-side fault injection for tests: after this many rounds the step call
+    // reports a (fake) device error instead of launching (0: off); set from
+    // AH_FAKE_DEVICE_FAILURE_AFTER_ROUNDS at creation
+    long long fail_after_rounds = 0, rounds_done = 0;
+    bool broken = false;      // the worker stopped after a device error
 
     void run();
 };
@@ -461,6 +467,30 @@ void ah_server::run()
     cudaSetDevice(device);
     std::vector<Lat *> loaded;
     bool dirty = true;
+    // the device failed: every queued or running request fails with its error
+    // (pollers see AH_ERR_CUDA instead of waiting) and the worker stops
+    auto fail_all = [&](cudaError_t e) {
+        std::lock_guard<std::mutex> lk(mu);
+        const double t = now_s() - t_origin;
+        auto mark = [&](uint64_t id) {
+            Result &r = results[id];
+            if (r.state == RQ_PENDING || r.state == RQ_RUNNING) {
+                r.state = RQ_FAILED;
+                r.err = cudaGetErrorString(e);
+                r.t_done = t;
+            }
+        };
+        for (auto &L : active) {
+            mark(L->id);
+            if (L->mem) cudaFreeAsync(L->mem, eng.st);
+            used -= L->bytes;
+        }
+        active.clear();
+        for (auto &L : pending) mark(L->id);
+        pending.clear();
+        stop = true;
+        broken = true;
+    };
     while (true) {
         std::vector<std::unique_ptr<Lat>> admit;
         {
@@ -509,18 +539,23 @@ void ah_server::run()
         if (dirty) {
             loaded.clear();
             for (auto &L : active) loaded.push_back(L.get());
-            if (eng.load(loaded) != cudaSuccess) break;
+            const cudaError_t e = eng.load(loaded);
+            if (e != cudaSuccess) { fail_all(e); break; }
             dirty = false;
         }
         int R = kServerRound;
         for (auto *L : loaded) R = std::min(R, steps_to_event(*L));
-        cudaError_t e = eng.steps(R);
+        cudaError_t e = fail_after_rounds > 0 && rounds_done >= fail_after_rounds ? cudaErrorLaunchFailure
+                                                                                   : eng.steps(R);
         if (e == cudaSuccess) e = cudaStreamSynchronize(eng.st);
-        if (e != cudaSuccess) break;
-        for (auto *L : loaded) {
-            stats.site_updates += (double)L->nsites * std::min(R, L->nsteps - L->step);
-            advance_mirror(*L, R);
+        if (e != cudaSuccess) { fail_all(e); break; }
+        ++rounds_done;
+        {
+            std::lock_guard<std::mutex> lk(mu);
+            for (auto *L : loaded) stats.site_updates += (double)L->nsites * std::min(R, L->nsteps - L->step);
+            stats.launches = eng.launches;
         }
+        for (auto *L : loaded) advance_mirror(*L, R);
         // retire finished lattices with their final observables
         for (size_t i = 0; i < active.size();) {
             Lat &L = *active[i];
@@ -530,9 +565,11 @@ void ah_server::run()
             cudaFreeAsync(L.mem, eng.st);
             std::lock_guard<std::mutex> lk(mu);
             Result &r = results[L.id];
-            r.state = ds == AH_OK || ds == AH_ERR_NONFINITE ? RQ_DONE : RQ_FAILED;
-            r.obs = o;
-            r.t_done = now_s() - t_origin;
+            if (r.state != RQ_CANCELLED) {          // a cancel that arrived during its last round wins
+                r.state = ds == AH_OK || ds == AH_ERR_NONFINITE ? RQ_DONE : RQ_FAILED;
+                r.obs = o;
+                r.t_done = now_s() - t_origin;
+            }
             used -= L.bytes;
             stats.completed += 1;
             active.erase(active.begin() + i);
@@ -553,6 +590,7 @@ ah_status ah_server_create(size_t hbm_budget_bytes, int32_t max_slots, int32_t f
     s->budget = hbm_budget_bytes;
     s->max_slots = max_slots;
     s->t_origin = now_s();
+    if (const char *f = std::getenv("AH_FAKE_DEVICE_FAILURE_AFTER_ROUNDS")) s->fail_after_rounds = std::atoll(f);
     cudaGetDevice(&s->device);
     cudaError_t e = s->eng.init(!(flags & AH_BATCH_NO_GRAPH));
     if (e == cudaSuccess) e = batch_shape_prepare(0, s->eng.num_sms, s->eng.st);
@@ -576,6 +614,7 @@ ah_status ah_server_submit(ah_server *s, const ah_config *cfg, uint64_t *req_id)
     L->bytes = lattice_bytes(*cfg);
     if (L->bytes > s->budget) return host_fail(AH_ERR_OOM, "request larger than the server's HBM budget");
     std::lock_guard<std::mutex> lk(s->mu);
+    if (s->broken) return host_fail(AH_ERR_CUDA, "the server stopped after a device error");
     L->id = s->next_id++;
     L->t_submit = now_s() - s->t_origin;
     ah_server::Result r{};
@@ -635,7 +674,6 @@ ah_status ah_server_stats_get(ah_server *s, ah_server_stats *out)
     out->running = (int32_t)s->active.size();
     out->queued = (int32_t)s->pending.size();
     out->hbm_used = (int64_t)s->used;
-    out->launches = s->eng.launches;
     return AH_OK;
 }
 

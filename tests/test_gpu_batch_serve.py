@@ -161,3 +161,37 @@ def test_server_budget_and_cancel():
         with pytest.raises(ah.AhError) as e:
             srv.poll(123456)
         assert e.value.status == ah.AH_ERR_NOTFOUND
+
+
+def test_server_device_failure_fails_every_request(monkeypatch):
+    """Failure detection without a GPU fault: the server's step call reports a
+    (host-side fake) device error after two rounds; every running and queued
+    request then fails with AH_ERR_CUDA instead of staying busy, later
+    submissions are refused with AH_ERR_CUDA, and the server shuts down cleanly."""
+    monkeypatch.setenv("AH_FAKE_DEVICE_FAILURE_AFTER_ROUNDS", "2")
+    srv = ah.Server(hbm_budget_bytes=8 << 30, max_slots=2)
+    monkeypatch.delenv("AH_FAKE_DEVICE_FAILURE_AFTER_ROUNDS")
+    try:
+        ids = [srv.submit(ah.config(48, seed=70 + i)) for i in range(5)]    # 310 steps each: many rounds
+        for rid in ids:
+            t0 = time.time()
+            while True:
+                try:
+                    r = srv.poll(rid)
+                except ah.AhError as e:
+                    assert e.status == ah.AH_ERR_CUDA
+                    break
+                assert r is None, "a request completed although the device failed"
+                assert time.time() - t0 < 60
+                time.sleep(0.005)
+        st = srv.stats()
+        assert st["running"] == 0 and st["queued"] == 0 and st["hbm_used"] == 0
+        with pytest.raises(ah.AhError) as e:
+            srv.submit(ah.config(16))
+        assert e.value.status == ah.AH_ERR_CUDA
+    finally:
+        srv.close()
+    # a fresh server on the same device works
+    with ah.Server(hbm_budget_bytes=8 << 30, max_slots=2) as ok:
+        obs, _, _ = wait_done(ok, ok.submit(ah.config(16, seed=1)))
+        assert obs["nonfinite"] == 0

@@ -697,7 +697,7 @@ ah_status ah_autotune(ah_sim *h, int32_t trial_steps, int32_t *chosen)
     AH_CUDA(cudaEventCreate(&e0));
     AH_CUDA(cudaEventCreate(&e1));
     const int nv = n_variants(h->cfg.precision);
-    int best = 0;
+    int best = -1;
     float best_ms = 0.0f;
     for (int v = 0; v < nv && st == AH_OK; ++v) {
         if (!variant_ok(h, v)) continue;
@@ -713,12 +713,13 @@ ah_status ah_autotune(ah_sim *h, int32_t trial_steps, int32_t *chosen)
         if (ce != cudaSuccess) { st = fail(AH_ERR_CUDA, "autotune: %s", cudaGetErrorString(ce)); break; }
         float ms = 0.0f;
         cudaEventElapsedTime(&ms, e0, e1);
-        if (v == 0 || ms < best_ms) { best = v; best_ms = ms; }
+        if (best < 0 || ms < best_ms) { best = v; best_ms = ms; }
         if ((st = check_device_error(h)) != AH_OK) break;
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (st != AH_OK) return st;
+    if (best < 0) return fail(AH_ERR_ARG, "no step shape available for N=%d", h->N);
     h->variant = best;
     tune_cache_put(h, best);
     AH_CUDA(write_initial_state(h));

@@ -25,6 +25,7 @@
 #include <new>
 #include <string>
 #include <thread>
+#include <tuple>
 #include <vector>
 
 #include "../../include/ah.h"
@@ -130,7 +131,8 @@ struct Engine {
     DiagList list{};
     unsigned long long *h_count = nullptr;
     int diag_blocks = 0;
-    std::map<int, cudaGraphExec_t> graphs;   // R -> R batched steps
+    // (shape, R, lattices loaded) -> R batched steps
+    std::map<std::tuple<int, int, int>, cudaGraphExec_t> graphs;
     bool use_graph = true;
     long long launches = 0;
     int rounds = 0;
@@ -244,7 +246,7 @@ struct Engine {
             }
             return cudaSuccess;
         }
-        auto key = R * 4096 + nlat_loaded;
+        const auto key = std::make_tuple(shape, R, nlat_loaded);
         auto it = graphs.find(key);
         if (it == graphs.end()) {
             cudaGraph_t g;

@@ -349,6 +349,7 @@ extern "C" ah_status ah_batch_run(const ah_config *cfgs, int32_t count, int32_t 
     int best = 0;
     if (flags & AH_BATCH_AUTOTUNE) {
         float best_ms = 0.0f;
+        bool timed = false;
         cudaEvent_t a, b;
         cudaEventCreate(&a);
         cudaEventCreate(&b);
@@ -361,14 +362,14 @@ extern "C" ah_status ah_batch_run(const ah_config *cfgs, int32_t count, int32_t 
             if (e == cudaSuccess) e = eng.load(ptrs);
             if (e != cudaSuccess) break;
             eng.use_graph = false;
-            eng.steps(1);
-            cudaEventRecord(a, eng.st);
-            eng.steps(2);
-            cudaEventRecord(b, eng.st);
-            e = cudaEventSynchronize(b);
+            e = eng.steps(1);
+            if (e == cudaSuccess) e = cudaEventRecord(a, eng.st);
+            if (e == cudaSuccess) e = eng.steps(2);
+            if (e == cudaSuccess) e = cudaEventRecord(b, eng.st);
+            if (e == cudaSuccess) e = cudaEventSynchronize(b);
             float ms = 0.0f;
-            cudaEventElapsedTime(&ms, a, b);
-            if (s == 0 || ms < best_ms) { best = s; best_ms = ms; }
+            if (e == cudaSuccess) cudaEventElapsedTime(&ms, a, b);
+            if (e == cudaSuccess && (!timed || ms < best_ms)) { best = s; best_ms = ms; timed = true; }
             for (auto &L : lats)
                 if (e == cudaSuccess) e = lat_reinit(L, eng.st);
         }

@@ -323,6 +323,12 @@ class Server:
     def __exit__(self, *a):
         self.close()
 
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
 
 # ---- convenience ------------------------------------------------------------------
 def config(N: int, **kw) -> ah_config:

@@ -434,3 +434,32 @@ def test_state_larger_than_hbm_reports_oom_and_the_device_stays_usable():
     with sim(16, ah.AH_FP32, ah.AH_KERNEL_FUSED) as g:
         g.step(3)
         assert g.observables()["nonfinite"] == 0
+
+
+def test_two_simulations_from_two_threads_match_sequential_runs():
+    """Host-side thread safety: two simulations (different sizes, one autotuned)
+    created, stepped and measured from two threads at once give bit for bit the
+    fields and observables of the same runs done one after the other."""
+    import threading
+
+    def run(N, seed, flags, out, key):
+        with sim(N, ah.AH_FP32, ah.AH_KERNEL_FUSED, ah.AH_MATTER, 1.0, seed=seed, flags=flags) as g:
+            v = g.info["variant"]
+            g.step(15)
+            o = g.observables()
+            out[key] = (v, g.fields(), o["sums"], o["wind_abs_plane"])
+
+    jobs = [(40, 3, ah.AH_FLAG_AUTOTUNE), (27, 4, 0)]
+    seq, par = {}, {}
+    for i, (N, seed, fl) in enumerate(jobs):
+        run(N, seed, fl, seq, i)
+    threads = [threading.Thread(target=run, args=(N, seed, fl, par, i)) for i, (N, seed, fl) in enumerate(jobs)]
+    for t in threads:
+        t.start()
+    for t in threads:
+        t.join()
+    for i in range(len(jobs)):
+        vs, fs, ss, ws = seq[i]
+        vp, fp, sp, wp = par[i]
+        assert vs == vp
+        assert np.array_equal(fs, fp) and ss == sp and ws == wp, i

@@ -39,6 +39,10 @@ WORKLOADS = {
                                "256^3 FP32 state, radiation era a~tau, s=0, seed 2, diagnostics every 20 steps"),
     "lattice256_fp64_rad_s0": (256, 1, 1, 0.0, 2, 20,
                                "256^3 FP64 state, radiation era a~tau, s=0, seed 2, diagnostics every 20 steps"),
+    # the paper's own production case (Sec. 3-4: 512^3, radiation, s=0, diagnostics
+    # every 5 steps), for comparison with its Quadro P5000 figures
+    "lattice512_fp32_rad_s0_diag5": (512, 0, 1, 0.0, 1, 5,
+                                     "512^3 FP32 state, radiation era a~tau, s=0, seed 1, diagnostics every 5 steps"),
     # profiling-sized case of the default workload (3.2 GB state, larger than L2)
     "lattice384_fp32_matter_s1": (384, 0, 2, 1.0, 3, 50,
                                   "384^3 FP32 state, matter era a~tau^2, s=1, seed 3, diagnostics every 50 steps"),

@@ -60,11 +60,15 @@ __device__ __forceinline__ cpx<real> plaq2(cpx<real> a, cpx<real> b, cpx<real> c
     const cpx<real> ab = mul(a, b), cd = mul(c, d);
     return { ab.r * cd.r + ab.i * cd.i, ab.i * cd.r - ab.r * cd.i };
 }
-// 1 - cos Xi from e^{i Xi} = (c, s) without cancellation
+// 1 - cos Xi from e^{i Xi} = (c, s) without cancellation (in FP32 the
+// quotient by the fast approximate division, a few ulp)
 template <typename real>
 __device__ __forceinline__ real one_minus_cos(cpx<real> e)
 {
-    return e.r > real(0) ? e.i * e.i / (real(1) + e.r) : real(1) - e.r;
+    if constexpr (sizeof(real) == 4)
+        return e.r > 0.f ? __fdividef(e.i * e.i, 1.f + e.r) : 1.f - e.r;
+    else
+        return e.r > 0.0 ? e.i * e.i / (1.0 + e.r) : 1.0 - e.r;
 }
 
 __device__ __forceinline__ int wrapm(int a, int N)
@@ -343,9 +347,11 @@ __device__ __forceinline__ void fused_tile(const View<real> &v, int N, int zc, c
                 p13[m] = plaq(U0[e], U0[2 * NE + e + 1], U1p[e], U0[2 * NE + e]);
                 p23[m] = plaq(U0[NE + e], U0[2 * NE + e + EX], U1p[NE + e], U0[2 * NE + e]);
             }
-            sP[p] = p12[m];
-            sP[G::NP + p] = p13[m];
-            sP[2 * G::NP + p] = p23[m];
+            if constexpr (STEP) {              // the sines feed only the E kick
+                sP[p] = p12[m];
+                sP[G::NP + p] = p13[m];
+                sP[2 * G::NP + p] = p23[m];
+            }
         }
         if constexpr (DIAG) {
             // own edges of plane z, then the right column's d = 2, 3 and the
@@ -369,7 +375,7 @@ __device__ __forceinline__ void fused_tile(const View<real> &v, int N, int zc, c
                 sE[2 * NE + e] = edge(F0[e], U0[2 * NE + e], F1[e]);
             }
         }
-        if (tid < G::NPHALO) {
+        if (STEP && tid < G::NPHALO) {
             const int px = tid < PX ? tid : 0, py = tid < PX ? 0 : tid - PX + 1;
             const int e = py * EX + px, p = py * PX + px;
             sP[p] = plaq(U0[e], U0[NE + e + 1], U0[e + EX], U0[NE + e]);
@@ -427,7 +433,7 @@ __device__ __forceinline__ void fused_tile(const View<real> &v, int N, int zc, c
                 const real B = k_b * bcos[m];
                 const real L = K - G2 - V + Eel - B;
                 const real rho = K + G2 + V + Eel + B;
-                const real pp = K - G2 / real(3) - V + (Eel + B) / real(3);
+                const real pp = K - G2 * real(1.0 / 3.0) - V + (Eel + B) * real(1.0 / 3.0);
                 dacc[0].add(L); dacc[1].add(rho); dacc[2].add(pp); dacc[3].add(K); dacc[4].add(G2);
                 dacc[5].add(V); dacc[6].add(Eel); dacc[7].add(B); dacc[8].add(K * V); dacc[9].add(G2 * V);
                 dacc[10].add(K * L); dacc[11].add(G2 * L); dacc[12].add(pp * L); dacc[13].add(rho * L);

@@ -6,8 +6,11 @@ leapfrog steps (Eqs. up_pi, up_E, up_phi, up_A of arXiv:1809.00995) followed by
 one diagnostics pass (xi_L, xi_W, <v^2>_V, <v^2>_L, <v^2>_omega, Gauss residual).
 The default workload is a 1024^3 FP32 lattice in the matter era with s = 1,
 diagnostics every 50 steps (FP64 reductions); the metric is site-updates/s.
+FP32 workloads with an even diagnostics interval run two leapfrog steps per
+kernel pass (AH_FLAG_TWO_STEP, temporal blocking); `--single-step` runs one.
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME] [--impl ours|reference]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME] [--single-step]
+                  [--impl ours|reference]
 
 With N > 1 (torchrun, one rank per GPU) every rank evolves its own lattice
 (independent seeds): replicas, no collective on the data path; the barrier and
@@ -49,7 +52,7 @@ WORKLOADS = {
 }
 DEFAULT = "lattice1024_fp32_matter_s1"
 BYTES_PER_SITE = {0: 80, 1: 160}      # one read + one write of the 10-real state
-TRAFFIC_FILE = os.path.join(ROOT, "profiles", "fused_step_traffic.json")
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "fused_traffic.json")
 
 
 def parse():
@@ -63,6 +66,9 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-ensemble measurement")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving measurement")
+    ap.add_argument("--single-step", action="store_true",
+                    help="one leapfrog step per kernel pass (default for FP32 workloads with an even "
+                         "diagnostics interval: AH_FLAG_TWO_STEP, two steps per pass)")
     ap.add_argument("--variant", default=None,
                     help="fused-step shape by name (default: autotuned), e.g. ty8_b4")
     ap.add_argument("--serve-requests", type=int, default=40,
@@ -99,19 +105,27 @@ def peaks():
         return 6800.0, "fallback (6.8 TB/s)"
 
 
-def source_hash(path):
-    with open(path, "rb") as f:
-        return hashlib.sha256(f.read()).hexdigest()[:16]
+# sources of the single-step and the two-step kernel: a traffic record is void
+# once any of its kernel's sources changes
+KERNEL_SOURCES = {"k_fused": ("k_fused.cu", "fused_common.cuh", "sincos32.cuh"),
+                  "k_fused2": ("k_fused2.cu", "fused_common.cuh", "sincos32.cuh")}
 
 
-def traffic_per_launch(n_sites, variant):
-    """DRAM bytes per launch of the fused step from the committed ncu summary, if it
-    was taken on the current kernel source and on the shape that ran."""
+def kernel_source_hash(kernel):
+    h = hashlib.sha256()
+    for name in KERNEL_SOURCES[kernel]:
+        with open(os.path.join(ROOT, "paper_1809_00995_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def traffic_per_launch(n_sites, kernel, variant):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, if it was
+    taken on the current kernel sources and on the shape that ran."""
     try:
         with open(TRAFFIC_FILE) as f:
-            d = json.load(f)
-        src = os.path.join(ROOT, "paper_1809_00995_gb300", "csrc", "k_fused.cu")
-        if d.get("k_fused_sha256_16") != source_hash(src) or d.get("variant") != variant:
+            d = json.load(f)[kernel]
+        if d.get("sources_sha256_16") != kernel_source_hash(kernel) or d.get("variant") != variant:
             return None
         return d["dram_bytes_per_site"] * n_sites
     except Exception:
@@ -341,11 +355,15 @@ def main():
     N, prec, era, s, seed, diag_every, desc = WORKLOADS[wl]
     n_sites = N ** 3
     stream = torch.cuda.Stream()
+    # two leapfrog steps per kernel pass (temporal blocking) where the library
+    # offers it (FP32) and the diagnostics interval is a whole number of passes
+    two_step = prec == 0 and diag_every % 2 == 0 and not a.single_step
+    mode = ah.AH_FLAG_TWO_STEP if two_step else 0
     g = ah.Sim(N, precision=prec, kernel=ah.AH_KERNEL_FUSED, era=era, s=s, seed=seed + 1000 * rank,
-               flags=0 if a.variant else ah.AH_FLAG_AUTOTUNE)
+               flags=mode | (0 if a.variant else ah.AH_FLAG_AUTOTUNE))
     if a.variant:
         names = {}
-        for v in range(ah.ah_variant_count(prec)):
+        for v in range(g.info["n_variants"]):
             try:
                 g.set_variant(v)
                 names[g.info["variant_name"]] = v
@@ -402,7 +420,7 @@ def main():
     barrier()
     t0 = time.perf_counter()
     cfg_e2e = ah.config(N, precision=prec, kernel=ah.AH_KERNEL_FUSED, era=era, s=s, seed=seed + 1000 * rank,
-                        flags=0 if a.variant else ah.AH_FLAG_AUTOTUNE)
+                        flags=mode | (0 if a.variant else ah.AH_FLAG_AUTOTUNE))
     h = ah.ah_create_ex(cfg_e2e)
     try:
         if a.variant:
@@ -417,16 +435,28 @@ def main():
     d2h = ctypes.sizeof(ah.ah_obs)
     final_obs = obs_e2e
 
-    avg_launch_s = step_ms / 1e3 / (a.steps * diag_every)
-    alg_bytes = BYTES_PER_SITE[prec] * n_sites
+    # one launch = one leapfrog step, or two in two-step mode.  Algorithmic
+    # bytes: 80 B (FP32) / 160 B (FP64) per site-update whatever the kernel, so
+    # a two-step launch counts 2 x that; it moves the state once, so its
+    # `achieved` is an effective bandwidth and its DRAM traffic is about half.
+    steps_per_launch = 2 if two_step else 1
+    avg_launch_s = step_ms / 1e3 / (a.steps * diag_every) * steps_per_launch
+    alg_bytes = BYTES_PER_SITE[prec] * n_sites * steps_per_launch
     peak, peak_src = peaks()
     achieved = alg_bytes / avg_launch_s / 1e9
-    tr = traffic_per_launch(n_sites, variant_name)
+    kname = "k_fused2" if two_step else "k_fused"
+    tr = traffic_per_launch(n_sites, kname, variant_name)
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": tr,
-                "kernel": "fused step, shape %s (one leapfrog step)" % variant_name, "peak_source": peak_src,
+                "kernel": ("fused step, shape %s (one leapfrog step per launch)" % variant_name if not two_step else
+                           "two-step fused kernel, shape %s (two leapfrog steps per launch)" % variant_name),
+                "peak_source": peak_src,
                 "alg_bytes_per_launch": alg_bytes, "avg_launch_ms": avg_launch_s * 1e3,
                 "step_share_of_time": step_ms / t_ms}
+    if two_step:
+        roofline["effective"] = True
+        roofline["dram_state_bytes_per_launch"] = BYTES_PER_SITE[prec] * n_sites
+        roofline["dram_frac"] = BYTES_PER_SITE[prec] * n_sites / avg_launch_s / 1e9 / peak
 
     plain = None
     if rank == 0 and not a.no_plain:
@@ -469,6 +499,7 @@ def main():
             "scaling": "weak", "vs_baseline": None, "dtype": "f32" if prec == 0 else "f64", "data": "synthetic",
             "config": {"workload": wl, "description": desc, "N": N, "diag_every": diag_every,
                        "leapfrog_steps_per_bench_step": diag_every,
+                       "leapfrog_steps_per_launch": steps_per_launch,
                        "l2": "inputs larger than L2 (%.1f GB state)" % (info["state_bytes"] / 1e9),
                        "parallelism": "replicas" if world > 1 else "single"},
             "hbm_gbs_effective": achieved,
@@ -479,7 +510,7 @@ def main():
                     "d2h_bytes_per_step": d2h, "h2d_bytes_per_job": ctypes.sizeof(ah.ah_config),
                     "timed": "ah_create_ex + %d x (ah_step(%d) + ah_observables to host) + ah_destroy, host clock"
                              % (a.steps, diag_every)},
-            "gpu_launches": a.steps * (diag_every * info["step_launches"] + 3),
+            "gpu_launches": a.steps * (diag_every * info["step_launches"] // steps_per_launch + 3),
             "batch": batch,
             "serve": serve,
             "clocks": clocks,

@@ -67,10 +67,11 @@ enum { AH_KERNEL_AUTO = 0, AH_KERNEL_PLAIN = 1, AH_KERNEL_FUSED = 2 };
  *  precision (accumulated in FP64), the Gauss residual in FP64, and windings by
  *  sign carries that equal the FP64 arctangent formula, with the plaquettes
  *  near a branch cut re-evaluated in FP64. */
-enum { AH_FLAG_EXACT_DIAG = 1, AH_FLAG_AUTOTUNE = 2, AH_FLAG_WRAP_THETA = 4, AH_FLAG_CORE_GROWTH = 8 };
+enum { AH_FLAG_EXACT_DIAG = 1, AH_FLAG_AUTOTUNE = 2, AH_FLAG_WRAP_THETA = 4, AH_FLAG_CORE_GROWTH = 8,
+       AH_FLAG_TWO_STEP = 16 };
 /* AUTOTUNE: at creation, time every compile-time shape of the fused step on
  * the initial state (then re-initialise it) and keep the fastest; results are
- * cached per (device, N, precision) for the life of the process.
+ * cached per (device, N, precision, two-step mode) for the life of the process.
  * WRAP_THETA: after every drift (Eq. up_A) a link phase with |theta| > pi is
  * replaced by theta - 2 pi k, k the nearest integer to theta / 2 pi, so that
  * theta stays in [-pi, pi] (to one rounding) and an FP32 state keeps its
@@ -83,7 +84,18 @@ enum { AH_FLAG_EXACT_DIAG = 1, AH_FLAG_AUTOTUNE = 2, AH_FLAG_WRAP_THETA = 4, AH_
  * tau < tau_ref (s < 0 grows the width) and 1 from tau_ref on.  Since
  * a(tau_ref) = 1, e and lambda equal e0 and lambda0 on both sides of the
  * switch, so the couplings are continuous there.  Every coupling of a step
- * (at tau_n and tau_n +- dt/2) takes the exponent of its own time. */
+ * (at tau_n and tau_n +- dt/2) takes the exponent of its own time.
+ * TWO_STEP (FP32, fused kernel only): ah_step advances pairs of steps with
+ * one kernel pass each (temporal blocking: the state is read and written once
+ * per two steps, 40 B per site-update instead of 80), and an odd last step
+ * with the single-step kernel.  Each step evaluates the same formulas as a
+ * single step; results agree to FP32 rounding (multiply-adds may be fused
+ * differently).  Pi and E are then kept in two buffer sets (one read, one
+ * written), so the state takes 20 instead of 15 arrays of N^3 reals; in this
+ * mode ah_set_variant, ah_autotune and ah_info.variant / n_variants /
+ * variant_name refer to the two-step shapes, and the TMA-fed single-step
+ * shapes are not available.  Refused (AH_ERR_ARG) for FP64 and for
+ * AH_KERNEL_PLAIN. */
 
 typedef struct ah_config {
     int32_t N;            /* lattice side, 4 <= N <= 2048                         */

@@ -26,7 +26,7 @@ AH_ERR_NONFINITE, AH_ERR_TIMEOUT, AH_ERR_BUSY, AH_ERR_CANCELLED, AH_ERR_NOTFOUND
 AH_MINKOWSKI, AH_RADIATION, AH_MATTER = 0, 1, 2
 AH_FP32, AH_FP64 = 0, 1
 AH_KERNEL_AUTO, AH_KERNEL_PLAIN, AH_KERNEL_FUSED = 0, 1, 2
-AH_FLAG_EXACT_DIAG, AH_FLAG_AUTOTUNE, AH_FLAG_WRAP_THETA, AH_FLAG_CORE_GROWTH = 1, 2, 4, 8
+AH_FLAG_EXACT_DIAG, AH_FLAG_AUTOTUNE, AH_FLAG_WRAP_THETA, AH_FLAG_CORE_GROWTH, AH_FLAG_TWO_STEP = 1, 2, 4, 8, 16
 AH_BATCH_AUTOTUNE, AH_BATCH_NO_GRAPH = 1, 2
 
 SUM_NAMES = ("L", "rho", "p", "K", "G2", "V", "Eel", "B", "KV", "G2V", "KL", "G2L", "pL", "rhoL",

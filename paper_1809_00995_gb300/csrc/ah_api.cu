@@ -130,6 +130,8 @@ struct ah_sim {
     DiagList list;
     int diag_blocks;
     int variant;
+    int variant2;      // two-step shape (AH_FLAG_TWO_STEP)
+    bool two_step;
     bool pristine;     // state is the freshly initialised random-phase state
     bool tma_ready;    // tensor maps built (FP32, N % 32 == 0)
     TmaMaps tmaps[2];  // per read buffer (phi/theta ping-pong index)
@@ -142,7 +144,7 @@ struct ah_sim {
 namespace {
 
 template <typename real>
-void carve(Fields<real> &F, char *base, size_t n)
+void carve(Fields<real> &F, char *base, size_t n, bool spare = false)
 {
     real *p = (real *)base;
     const size_t pn = padded(n);
@@ -154,6 +156,10 @@ void carve(Fields<real> &F, char *base, size_t n)
     F.pir = p; p += pn;
     F.pii = p; p += pn;
     for (int d = 0; d < 3; ++d) { F.el[d] = p; p += pn; }
+    for (int k = 0; k < 5; ++k) {
+        F.spare[k] = spare ? p : nullptr;
+        if (spare) p += pn;
+    }
 }
 
 template <typename real>
@@ -181,8 +187,11 @@ ah_status validate(const ah_config &c)
         return fail(AH_ERR_ARG, "unknown precision %d", c.precision);
     if (c.kernel < AH_KERNEL_AUTO || c.kernel > AH_KERNEL_FUSED)
         return fail(AH_ERR_ARG, "unknown kernel %d", c.kernel);
-    if (c.flags & ~(AH_FLAG_EXACT_DIAG | AH_FLAG_AUTOTUNE | AH_FLAG_WRAP_THETA | AH_FLAG_CORE_GROWTH))
+    if (c.flags & ~(AH_FLAG_EXACT_DIAG | AH_FLAG_AUTOTUNE | AH_FLAG_WRAP_THETA | AH_FLAG_CORE_GROWTH |
+                    AH_FLAG_TWO_STEP))
         return fail(AH_ERR_ARG, "unknown flags 0x%x", c.flags);
+    if ((c.flags & AH_FLAG_TWO_STEP) && (c.precision != AH_FP32 || c.kernel == AH_KERNEL_PLAIN))
+        return fail(AH_ERR_ARG, "AH_FLAG_TWO_STEP needs FP32 and the fused kernel");
     if (!std::isfinite(c.s)) return fail(AH_ERR_ARG, "s must be finite");
     if (c.era != AH_MINKOWSKI && !(c.tau0 > 0)) return fail(AH_ERR_ARG, "tau0 must be > 0");
     if (!(c.tau_ref > 0)) return fail(AH_ERR_ARG, "tau_ref must be > 0");
@@ -233,6 +242,7 @@ int family(const ah_sim *h, int v, int *idx)
 }
 bool variant_ok(const ah_sim *h, int v)
 {
+    if (h->two_step) return v >= 0 && v < fused2_variant_count();
     if (v < 0 || v >= n_variants(h->cfg.precision)) return false;
     int i;
     switch (family(h, v, &i)) {
@@ -244,6 +254,7 @@ bool variant_ok(const ah_sim *h, int v)
 }
 const char *variant_name(const ah_sim *h, int v)
 {
+    if (h->two_step) return fused2_variant_name(v);
     if (h->cfg.precision == AH_FP64) return fused_variant_name<double>(v);
     int i;
     switch (family(h, v, &i)) {
@@ -275,6 +286,29 @@ ah_status do_step(ah_sim *h, int64_t n)
         AH_CUDA(launch_fused_step<real>(make_view(F, h->cur, true), h->N, k, h->variant, h->stream));
         h->cur ^= 1;
     }
+    return AH_OK;
+}
+
+// Steps n and n + 1 in one pass (AH_FLAG_TWO_STEP): phi, theta go to the
+// other ping-pong buffer, Pi and E to the spare set, which then becomes the
+// current one.
+ah_status do_step2(ah_sim *h, int64_t n)
+{
+    Fields<float> &F = h->f32;
+    View2<float> v;
+    const int o = 1 - h->cur;
+    v.phr = F.phr[h->cur]; v.phi = F.phi[h->cur];
+    v.th1 = F.th[h->cur][0]; v.th2 = F.th[h->cur][1]; v.th3 = F.th[h->cur][2];
+    v.pir = F.pir; v.pii = F.pii; v.e1 = F.el[0]; v.e2 = F.el[1]; v.e3 = F.el[2];
+    v.ophr = F.phr[o]; v.ophi = F.phi[o];
+    v.oth1 = F.th[o][0]; v.oth2 = F.th[o][1]; v.oth3 = F.th[o][2];
+    v.opir = F.spare[0]; v.opii = F.spare[1]; v.oe1 = F.spare[2]; v.oe2 = F.spare[3]; v.oe3 = F.spare[4];
+    AH_CUDA(launch_fused2_step(v, h->N, kick_coef<float>(h->cfg, n), kick_coef<float>(h->cfg, n + 1), h->variant2,
+                               h->stream));
+    h->cur = o;
+    std::swap(F.pir, F.spare[0]);
+    std::swap(F.pii, F.spare[1]);
+    for (int d = 0; d < 3; ++d) std::swap(F.el[d], F.spare[2 + d]);
     return AH_OK;
 }
 
@@ -376,20 +410,20 @@ cudaError_t write_initial_state(ah_sim *h)
     return launch_init_phase<double>(h->f64.phr[0], h->f64.phi[0], h->N, h->cfg.seed, h->cfg.sigma, h->stream);
 }
 
-// process-wide autotune results per (device, N, precision)
+// process-wide autotune results per (device, N, precision, two-step mode)
 std::mutex g_tune_mu;
-std::map<std::tuple<int, int, int>, int> g_tune;
+std::map<std::tuple<int, int, int, bool>, int> g_tune;
 
 int tune_cache_get(const ah_sim *h)
 {
     std::lock_guard<std::mutex> lk(g_tune_mu);
-    auto it = g_tune.find(std::make_tuple(h->device, h->N, h->cfg.precision));
+    auto it = g_tune.find(std::make_tuple(h->device, h->N, h->cfg.precision, h->two_step));
     return it == g_tune.end() ? -1 : it->second;
 }
 void tune_cache_put(const ah_sim *h, int v)
 {
     std::lock_guard<std::mutex> lk(g_tune_mu);
-    g_tune[std::make_tuple(h->device, h->N, h->cfg.precision)] = v;
+    g_tune[std::make_tuple(h->device, h->N, h->cfg.precision, h->two_step)] = v;
 }
 
 ah_status enter(const ah_sim *h)
@@ -454,6 +488,8 @@ ah_status ah_create_ex(const ah_config *cfg, ah_sim **out)
     if (h->cfg.kernel == AH_KERNEL_AUTO) h->cfg.kernel = AH_KERNEL_FUSED;
     h->N = cfg->N;
     h->variant = cfg->precision == AH_FP32 ? fused_default_variant<float>() : fused_default_variant<double>();
+    h->two_step = (cfg->flags & AH_FLAG_TWO_STEP) != 0;
+    h->variant2 = fused2_default_variant();
     h->nsites = (long long)cfg->N * cfg->N * cfg->N;
     h->step = 0;
     h->cur = 0;
@@ -466,7 +502,7 @@ ah_status ah_create_ex(const ah_config *cfg, ah_sim **out)
     }
     h->own_stream = true;
     const size_t esz = cfg->precision == AH_FP32 ? sizeof(float) : sizeof(double);
-    h->dbytes = 15 * padded((size_t)h->nsites) * esz;
+    h->dbytes = (h->two_step ? 20 : 15) * padded((size_t)h->nsites) * esz;
     h->diag_blocks = diag_grid_blocks(h->num_sms);
     const int nparts = std::max(h->diag_blocks, fused_diag_ctas(h->N));
     // expected near-cut plaquettes: about 5e-5 of the 3 N^3 plaquettes in FP32
@@ -492,9 +528,10 @@ ah_status ah_create_ex(const ah_config *cfg, ah_sim **out)
         ah_destroy(h);
         return fail(AH_ERR_OOM, "allocation failed: %s", cudaGetErrorString(e));
     }
-    if (cfg->precision == AH_FP32) carve(h->f32, (char *)h->dmem, (size_t)h->nsites);
+    if (cfg->precision == AH_FP32) carve(h->f32, (char *)h->dmem, (size_t)h->nsites, h->two_step);
     else carve(h->f64, (char *)h->dmem, (size_t)h->nsites);
-    if (cfg->precision == AH_FP32 && tma_shape_ok(h->N)) {
+    // the TMA maps hold the Pi and E buffers, which the two-step mode swaps
+    if (cfg->precision == AH_FP32 && tma_shape_ok(h->N) && !h->two_step) {
         cudaError_t me = cudaSuccess;
         for (int b = 0; b < 2 && me == cudaSuccess; ++b) {
             const float *fs[5] = { h->f32.phr[b], h->f32.phi[b], h->f32.th[b][0], h->f32.th[b][1], h->f32.th[b][2] };
@@ -513,7 +550,7 @@ ah_status ah_create_ex(const ah_config *cfg, ah_sim **out)
     if (cfg->flags & AH_FLAG_AUTOTUNE) {
         const int cached = tune_cache_get(h);
         if (cached >= 0) {
-            h->variant = cached;
+            (h->two_step ? h->variant2 : h->variant) = cached;
         } else if ((st = ah_autotune(h, 3, nullptr)) != AH_OK) {
             ah_destroy(h);
             *out = nullptr;
@@ -548,7 +585,14 @@ ah_status ah_step(ah_sim *h, int64_t nsteps)
     if (st != AH_OK) return st;
     if (nsteps < 0) return fail(AH_ERR_ARG, "nsteps must be >= 0");
     if (nsteps > 0) h->pristine = false;
-    for (int64_t q = 0; q < nsteps; ++q) {
+    int64_t q = 0;
+    if (h->two_step) {
+        for (; q + 2 <= nsteps; q += 2) {
+            if ((st = do_step2(h, h->step)) != AH_OK) return st;
+            h->step += 2;
+        }
+    }
+    for (; q < nsteps; ++q) {
         st = h->cfg.precision == AH_FP32 ? do_step<float>(h, h->step) : do_step<double>(h, h->step);
         if (st != AH_OK) return st;
         ++h->step;
@@ -660,9 +704,9 @@ ah_status ah_get_info(const ah_sim *h, ah_info *out)
     out->state_bytes = (int64_t)h->dbytes;
     out->step_bytes = 20 * esz * h->nsites;
     out->step_launches = h->cfg.kernel == AH_KERNEL_PLAIN ? 3 : 1;
-    out->variant = h->variant;
-    out->n_variants = n_variants(h->cfg.precision);
-    const char *nm = variant_name(h, h->variant);
+    out->variant = h->two_step ? h->variant2 : h->variant;
+    out->n_variants = h->two_step ? fused2_variant_count() : n_variants(h->cfg.precision);
+    const char *nm = variant_name(h, out->variant);
     snprintf(out->variant_name, sizeof out->variant_name, "%s", h->cfg.kernel == AH_KERNEL_PLAIN ? "plain" : nm);
     return AH_OK;
 }
@@ -676,9 +720,9 @@ ah_status ah_set_variant(ah_sim *h, int32_t variant)
 {
     if (!h) return fail(AH_ERR_ARG, "null simulation handle");
     if (!variant_ok(h, variant))
-        return fail(AH_ERR_ARG, "variant %d not available (count %d, N=%d)", variant, n_variants(h->cfg.precision),
-                    h->N);
-    h->variant = variant;
+        return fail(AH_ERR_ARG, "variant %d not available (count %d, N=%d)", variant,
+                    h->two_step ? fused2_variant_count() : n_variants(h->cfg.precision), h->N);
+    (h->two_step ? h->variant2 : h->variant) = variant;
     return AH_OK;
 }
 
@@ -696,18 +740,23 @@ ah_status ah_autotune(ah_sim *h, int32_t trial_steps, int32_t *chosen)
     cudaEvent_t e0, e1;
     AH_CUDA(cudaEventCreate(&e0));
     AH_CUDA(cudaEventCreate(&e1));
-    const int nv = n_variants(h->cfg.precision);
+    const int nv = h->two_step ? fused2_variant_count() : n_variants(h->cfg.precision);
+    int &var = h->two_step ? h->variant2 : h->variant;
+    // one step (a step pair in two-step mode) of the shape being timed
+    auto trial = [h]() {
+        if (h->two_step) return do_step2(h, 0);
+        return h->cfg.precision == AH_FP32 ? do_step<float>(h, 0) : do_step<double>(h, 0);
+    };
     int best = -1;
     float best_ms = 0.0f;
     for (int v = 0; v < nv && st == AH_OK; ++v) {
         if (!variant_ok(h, v)) continue;
-        h->variant = v;
+        var = v;
         // one untimed step (first launch configures the kernel), then trial_steps timed
-        st = h->cfg.precision == AH_FP32 ? do_step<float>(h, 0) : do_step<double>(h, 0);
+        st = trial();
         if (st != AH_OK) break;
         cudaEventRecord(e0, h->stream);
-        for (int q = 0; q < trial_steps && st == AH_OK; ++q)
-            st = h->cfg.precision == AH_FP32 ? do_step<float>(h, 0) : do_step<double>(h, 0);
+        for (int q = 0; q < trial_steps && st == AH_OK; ++q) st = trial();
         cudaEventRecord(e1, h->stream);
         cudaError_t ce = cudaEventSynchronize(e1);
         if (ce != cudaSuccess) { st = fail(AH_ERR_CUDA, "autotune: %s", cudaGetErrorString(ce)); break; }
@@ -720,7 +769,7 @@ ah_status ah_autotune(ah_sim *h, int32_t trial_steps, int32_t *chosen)
     cudaEventDestroy(e1);
     if (st != AH_OK) return st;
     if (best < 0) return fail(AH_ERR_ARG, "no step shape available for N=%d", h->N);
-    h->variant = best;
+    var = best;
     tune_cache_put(h, best);
     AH_CUDA(write_initial_state(h));
     AH_CUDA(cudaStreamSynchronize(h->stream));

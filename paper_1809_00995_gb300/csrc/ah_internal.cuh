@@ -19,6 +19,9 @@ struct Fields {
     real *th[2][3];
     real *pir, *pii;
     real *el[3];
+    // second Pi, E set (Pi_r, Pi_i, E_1, E_2, E_3) for the two-step kernel,
+    // which reads one set and writes the other; null unless allocated
+    real *spare[5];
 };
 
 // View of one state for a kernel: the buffers it reads (and, for the fused
@@ -28,6 +31,16 @@ struct View {
     const real *phr, *phi, *th1, *th2, *th3;   // phi^n, theta^n
     real *pir, *pii, *e1, *e2, *e3;              // Pi, E (updated in place)
     real *ophr, *ophi, *oth1, *oth2, *oth3;      // phi^{n+1}, theta^{n+1}
+};
+
+// View of the two-step kernel: state n (phi^n, theta^n, Pi and E at n - 1/2)
+// is read from one set of buffers and state n + 2 written to another, with
+// nothing updated in place (a CTA recomputes the first step on a halo ring
+// that neighbouring CTAs overwrite with their second step).
+template <typename real>
+struct View2 {
+    const real *phr, *phi, *th1, *th2, *th3, *pir, *pii, *e1, *e2, *e3;
+    real *ophr, *ophi, *oth1, *oth2, *oth3, *opir, *opii, *oe1, *oe2, *oe3;
 };
 
 // Coefficients of one leapfrog step n (Eqs. up_pi and up_E), computed in FP64
@@ -134,6 +147,14 @@ template <typename real>
 bool fused_variant_ok(int variant, int N);
 template <typename real>
 int fused_default_variant();
+
+// Two leapfrog steps (coefficients c1 for step n, c2 for step n + 1) in one
+// pass, FP32; shape `variant` in [0, fused2_variant_count()).
+cudaError_t launch_fused2_step(const View2<float> &v, int N, const KickCoef<float> &c1, const KickCoef<float> &c2,
+                               int variant, cudaStream_t st);
+int fused2_variant_count();
+const char *fused2_variant_name(int variant);
+int fused2_default_variant();
 
 template <typename real>
 cudaError_t launch_diag(const View<real> &v, int N, Box b, const DiagCoef &c,

@@ -30,6 +30,7 @@
 #include "ah_internal.cuh"
 #include "diag_common.cuh"
 #include "sincos32.cuh"
+#include "fused_common.cuh"
 
 namespace ah {
 namespace {
@@ -38,28 +39,6 @@ namespace {
 // tile walk with nothing written back).
 enum { MODE_STEP = 0, MODE_DIAG = 1 };
 
-template <typename real>
-struct cpx { real r, i; };
-
-template <typename real>
-__device__ __forceinline__ cpx<real> mul(cpx<real> a, cpx<real> b)
-{
-    return { a.r * b.r - a.i * b.i, a.r * b.i + a.i * b.r };
-}
-// Im(a b conj(c) conj(d)) = Im((a b) conj(c d))
-template <typename real>
-__device__ __forceinline__ real plaq(cpx<real> a, cpx<real> b, cpx<real> c, cpx<real> d)
-{
-    const cpx<real> ab = mul(a, b), cd = mul(c, d);
-    return ab.i * cd.r - ab.r * cd.i;
-}
-// (a b) conj(c d) = e^{i Xi}: sine in .i, cosine in .r
-template <typename real>
-__device__ __forceinline__ cpx<real> plaq2(cpx<real> a, cpx<real> b, cpx<real> c, cpx<real> d)
-{
-    const cpx<real> ab = mul(a, b), cd = mul(c, d);
-    return { ab.r * cd.r + ab.i * cd.i, ab.i * cd.r - ab.r * cd.i };
-}
 // 1 - cos Xi from e^{i Xi} = (c, s) without cancellation (in FP32 the
 // quotient by the fast approximate division, a few ulp)
 template <typename real>
@@ -71,50 +50,8 @@ __device__ __forceinline__ real one_minus_cos(cpx<real> e)
         return e.r > 0.0 ? e.i * e.i / (1.0 + e.r) : 1.0 - e.r;
 }
 
-__device__ __forceinline__ int wrapm(int a, int N)
-{
-    a %= N;
-    return a < 0 ? a + N : a;
-}
-
-template <typename real, int TY, int RX>
-struct Geo {
-    static constexpr int TX = 32 * RX, NT = 256, RY = TY / 8, NS = RX * RY;
-    static constexpr int EX = TX + 2, EY = TY + 2, NE = EX * EY;
-    static constexpr int NHALO = 2 * EX + 2 * TY;
-    static constexpr int PX = TX + 1, PY = TY + 1, NP = PX * PY;
-    static constexpr int NPHALO = PX + TY;
-    static constexpr size_t smem = sizeof(cpx<real>) * (2 * 3 * NE + 2 * NE) + sizeof(real) * 3 * NP;
-    // MODE_DIAG: the three scaled edge products of each site of plane z
-    // (tile, right column, top row) after the step's arrays
-    static constexpr size_t diag_off = (smem + 15) / 16 * 16;
-    static constexpr size_t smem_diag = diag_off + sizeof(cpx<real>) * 3 * NE;
-    static_assert(TY % 8 == 0 && NHALO <= NT && NPHALO <= NT && TX + TY <= NT, "tile shape");
-};
-
-// RX consecutive reals of one row (vector access when RX = 2; the pair never
-// straddles the end of a row because N is even for these shapes).
-template <typename real, int RX> struct Row;
-template <typename real> struct Row<real, 1> {
-    static __device__ __forceinline__ void ld(const real *p, real *o) { o[0] = *p; }
-    static __device__ __forceinline__ void st(real *p, const real *i) { *p = i[0]; }
-};
-template <> struct Row<float, 2> {
-    static __device__ __forceinline__ void ld(const float *p, float *o)
-    { const float2 t = *reinterpret_cast<const float2 *>(p); o[0] = t.x; o[1] = t.y; }
-    static __device__ __forceinline__ void st(float *p, const float *i)
-    { *reinterpret_cast<float2 *>(p) = make_float2(i[0], i[1]); }
-};
-template <> struct Row<double, 2> {
-    static __device__ __forceinline__ void ld(const double *p, double *o)
-    { const double2 t = *reinterpret_cast<const double2 *>(p); o[0] = t.x; o[1] = t.y; }
-    static __device__ __forceinline__ void st(double *p, const double *i)
-    { *reinterpret_cast<double2 *>(p) = make_double2(i[0], i[1]); }
-};
-
 // Each thread owns RX consecutive sites in x times RY rows (y stride 8).
 // One work item of the fused step: tile (bx, by) of plane chunk bz, marched in z.
-template <int V> struct IC { static constexpr int value = V; };
 
 // IT: site-index type (int when N^3 < 2^31, so every field address is one
 // 32 x 32 -> 64-bit multiply-add; long long otherwise).
@@ -623,20 +560,16 @@ constexpr VariantInfo kVariants32[] = {
 constexpr VariantInfo kVariants64[] = { { 16, 1, 1, 16, false, "ty16_b1" }, { 8, 1, 2, 16, false, "ty8_b2" },
                                         { 8, 2, 1, 16, false, "x2_ty8_b1" }, { 8, 1, 2, 16, true, "ty8_b2_w" } };
 
-// Number of z chunks for `tiles` XY tiles of an N-plane lattice when `slots`
-// CTAs are resident at once: the grid runs in waves of `slots` CTAs, each CTA
-// marching its chunk plus two extra planes (the one below, read in the
-// prologue, and the prefetch past the top), so minimise
-// ceil(tiles n / slots) (ceil(N / n) + 2) over n with chunks of at least
-// min_chunk planes.
-int choose_chunks(int N, long long tiles, int slots, int min_chunk)
+}  // namespace
+
+int choose_chunks(int N, long long tiles, int slots, int min_chunk, int extra)
 {
     const int nmax = std::max(1, std::min(N / std::max(1, min_chunk), 64));
     int best = 1;
     long long best_cost = -1;
     for (int n = 1; n <= nmax; ++n) {
         const long long waves = (tiles * n + slots - 1) / slots;
-        const long long cost = waves * ((N + n - 1) / n + 2);
+        const long long cost = waves * ((N + n - 1) / n + extra);
         if (best_cost < 0 || cost < best_cost) {
             best_cost = cost;
             best = n;
@@ -656,6 +589,8 @@ int device_sm_count()
     }
     return n;
 }
+
+namespace {
 
 template <typename real, int TY, int RX, int MINB>
 cudaError_t launch_shape(const View<real> &v, int N, const KickCoef<real> &c, int min_chunk, bool wave_model,

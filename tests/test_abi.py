@@ -66,3 +66,13 @@ def test_binding_constants_match_the_header():
             assert getattr(ah, name) == int(val), name
             found += 1
     assert found >= 20 and ah.AH_FLAG_WRAP_THETA == 4
+
+
+def test_two_step_flag_refused_for_fp64_and_plain_without_gpu():
+    """AH_FLAG_TWO_STEP is an FP32 fused-kernel mode: other configurations are
+    refused by the argument check, before any device call."""
+    for prec, kern in [(ah.AH_FP64, ah.AH_KERNEL_FUSED), (ah.AH_FP32, ah.AH_KERNEL_PLAIN)]:
+        c = ah.config(8, precision=prec, kernel=kern, flags=ah.AH_FLAG_TWO_STEP)
+        with pytest.raises(ah.AhError) as e:
+            ah.ah_create_ex(c)
+        assert e.value.status == ah.AH_ERR_ARG and "TWO_STEP" in str(e.value)

@@ -269,7 +269,8 @@ __device__ __forceinline__ void fused_tile(const View<real> &v, int N, int zc, c
 
         // B: plaquette sines of plane z on the tile (own sites) and its low halos
         const cpx<real> *U0 = sU + bc * 3 * NE, *U1p = sU + bn * 3 * NE;
-        real p12[NS], p13[NS], p23[NS], bcos[NS];
+        real p12[NS], p13[NS], p23[NS];
+        [[maybe_unused]] real bcos[NS];          // MODE_DIAG: 1 - cos Xi summed over the three orientations
 #pragma unroll
         for (int m = 0; m < NS; ++m) {
             const int e = eix(m), p = pix(m);
@@ -352,7 +353,7 @@ __device__ __forceinline__ void fused_tile(const View<real> &v, int N, int zc, c
             const real ne1 = c.c_edamp * e1[m] + c.c_cur * cu1 - c.c_curl * cl1;
             const real ne2 = c.c_edamp * e2[m] + c.c_cur * cu2 - c.c_curl * cl2;
             const real ne3 = c.c_edamp * e3[m] + c.c_cur * cu3 - c.c_curl * cl3;
-            Z ez1[NS], ez2[NS];              // MODE_DIAG: own d = 1, 2 edges of plane z+1
+            [[maybe_unused]] Z ez1[NS], ez2[NS];   // MODE_DIAG: own d = 1, 2 edges of plane z+1
             if constexpr (DIAG) {
                 const cpx<real> *F1 = sF + bn * NE;
                 ez1[m] = edge(F1[e], U1p[e], F1[e + 1]);

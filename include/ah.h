@@ -215,13 +215,16 @@ double ah_get_tau(const ah_sim *sim);
 
 /* Information for measurement: bytes of device state, the algorithmic bytes
  * one leapfrog step must move (one read and one write of the 10-component
- * state: 80 B per site in FP32, 160 B in FP64), and the kernel in use. */
+ * state: 80 B per site in FP32, 160 B in FP64; in two-step mode a launch
+ * advances two steps with one read and one write, so the DRAM bytes per step
+ * are half of step_bytes), and the kernel in use. */
 typedef struct ah_info {
     int64_t N, n_sites;
     int32_t precision, kernel;
     int64_t state_bytes;
     int64_t step_bytes;
-    int64_t step_launches;   /* kernel launches per leapfrog step          */
+    int64_t step_launches;   /* kernel launches per leapfrog step (in
+                                two-step mode: per pair of steps)         */
     int32_t variant;         /* shape of the fused step in use             */
     int32_t n_variants;      /* shapes available for this precision        */
     char variant_name[32];

@@ -273,7 +273,11 @@ typedef struct ah_batch_stats {
  * series_len[i] receives the number produced (entries past series_cap are
  * dropped).  flags: AH_BATCH_AUTOTUNE (time each batched shape on the initial
  * states, then restore them), AH_BATCH_NO_GRAPH (plain launches).  stats may be
- * NULL.  Synchronous; all device memory is released before return. */
+ * NULL.  Synchronous; all device memory is released before return.  Of the
+ * per-lattice cfgs[i].flags, AH_FLAG_WRAP_THETA and AH_FLAG_CORE_GROWTH apply;
+ * AH_FLAG_AUTOTUNE, AH_FLAG_EXACT_DIAG and AH_FLAG_TWO_STEP have no effect (the
+ * batched kernel advances one step per launch, and the diagnostics are those of
+ * the whole-lattice pass).  The same holds for requests to the server. */
 ah_status ah_batch_run(const ah_config *cfgs, int32_t count, int32_t flags, ah_obs *series,
                        int64_t series_cap, int64_t *series_len, ah_batch_stats *stats);
 

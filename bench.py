@@ -70,7 +70,8 @@ def parse():
                     help="one leapfrog step per kernel pass (default for FP32 workloads with an even "
                          "diagnostics interval: AH_FLAG_TWO_STEP, two steps per pass)")
     ap.add_argument("--variant", default=None,
-                    help="fused-step shape by name (default: autotuned), e.g. ty8_b4")
+                    help="step-kernel shape by name (default: autotuned), e.g. ty8_b4_w, or two_ty8_b3 "
+                         "in two-step mode")
     ap.add_argument("--serve-requests", type=int, default=40,
                     help="requests of the serving run (500 for the full workload; 2 per second)")
     return ap.parse_args()
@@ -119,15 +120,17 @@ def kernel_source_hash(kernel):
     return h.hexdigest()[:16]
 
 
-def traffic_per_launch(n_sites, kernel, variant):
+def traffic_per_launch(N, kernel, variant):
     """DRAM bytes per launch of `kernel` from the committed ncu summary, if it was
-    taken on the current kernel sources and on the shape that ran."""
+    taken on the current kernel sources, on the shape that ran and on an N^3
+    lattice (the halo re-reads that L2 does not serve depend on the size)."""
     try:
         with open(TRAFFIC_FILE) as f:
             d = json.load(f)[kernel]
-        if d.get("sources_sha256_16") != kernel_source_hash(kernel) or d.get("variant") != variant:
+        if (d.get("sources_sha256_16") != kernel_source_hash(kernel) or d.get("variant") != variant
+                or d.get("N") != N):
             return None
-        return d["dram_bytes_per_site"] * n_sites
+        return d["dram_bytes_per_site"] * N ** 3
     except Exception:
         return None
 
@@ -445,7 +448,7 @@ def main():
     peak, peak_src = peaks()
     achieved = alg_bytes / avg_launch_s / 1e9
     kname = "k_fused2" if two_step else "k_fused"
-    tr = traffic_per_launch(n_sites, kname, variant_name)
+    tr = traffic_per_launch(N, kname, variant_name)
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": tr,
                 "kernel": ("fused step, shape %s (one leapfrog step per launch)" % variant_name if not two_step else

@@ -120,6 +120,12 @@ def kernel_source_hash(kernel):
     return h.hexdigest()[:16]
 
 
+def use_two_step(precision, diag_every, single_step=False):
+    """Two leapfrog steps per kernel pass (temporal blocking) where the library
+    offers it (FP32) and the diagnostics interval is a whole number of passes."""
+    return precision == 0 and diag_every % 2 == 0 and not single_step
+
+
 def traffic_per_launch(N, kernel, variant):
     """DRAM bytes per launch of `kernel` from the committed ncu summary, if it was
     taken on the current kernel sources, on the shape that ran and on an N^3
@@ -358,9 +364,7 @@ def main():
     N, prec, era, s, seed, diag_every, desc = WORKLOADS[wl]
     n_sites = N ** 3
     stream = torch.cuda.Stream()
-    # two leapfrog steps per kernel pass (temporal blocking) where the library
-    # offers it (FP32) and the diagnostics interval is a whole number of passes
-    two_step = prec == 0 and diag_every % 2 == 0 and not a.single_step
+    two_step = use_two_step(prec, diag_every, a.single_step)
     mode = ah.AH_FLAG_TWO_STEP if two_step else 0
     g = ah.Sim(N, precision=prec, kernel=ah.AH_KERNEL_FUSED, era=era, s=s, seed=seed + 1000 * rank,
                flags=mode | (0 if a.variant else ah.AH_FLAG_AUTOTUNE))

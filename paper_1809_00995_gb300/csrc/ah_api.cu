@@ -124,6 +124,7 @@ struct ah_sim {
     Fields<float> f32;
     Fields<double> f64;
     DiagPartial *partials;
+    int nparts;        // entries of partials before result
     DiagPartial *result;
     DiagPartial *host_result;
     unsigned long long *host_count;
@@ -337,7 +338,8 @@ ah_status do_diag(ah_sim *h, Box b, ah_obs *out)
     const bool exact = (h->cfg.flags & AH_FLAG_EXACT_DIAG) != 0;
     const bool whole = b.x0 == 0 && b.y0 == 0 && b.z0 == 0 && b.nx == h->N && b.ny == h->N && b.nz == h->N;
     if (whole && !exact)
-        AH_CUDA(launch_diag_whole<real>(v, h->N, dc, h->partials, h->result, h->list, h->diag_blocks, h->stream));
+        AH_CUDA(launch_diag_whole<real>(v, h->N, dc, h->partials, h->nparts, h->result, h->list, h->diag_blocks,
+                                        h->stream));
     else
         AH_CUDA(launch_diag<real>(v, h->N, b, dc, h->partials, h->diag_blocks, h->result, h->list, exact,
                                   h->stream));
@@ -505,6 +507,7 @@ ah_status ah_create_ex(const ah_config *cfg, ah_sim **out)
     h->dbytes = (h->two_step ? 20 : 15) * padded((size_t)h->nsites) * esz;
     h->diag_blocks = diag_grid_blocks(h->num_sms);
     const int nparts = std::max(h->diag_blocks, fused_diag_ctas(h->N));
+    h->nparts = nparts;
     // expected near-cut plaquettes: about 5e-5 of the 3 N^3 plaquettes in FP32
     h->list.capacity = std::max<long long>(1LL << 20, h->nsites * 3 / 2000);
     e = cudaMalloc(&h->dmem, h->dbytes);

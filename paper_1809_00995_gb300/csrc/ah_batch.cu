@@ -128,6 +128,7 @@ struct Engine {
     int cap_lat = 0;
     long long cap_items = 0;
     DiagPartial *d_partials = nullptr, *d_result = nullptr, *h_result = nullptr;
+    int nparts = 0;                    // entries of d_partials before d_result
     DiagList list{};
     unsigned long long *h_count = nullptr;
     int diag_blocks = 0;
@@ -145,8 +146,13 @@ struct Engine {
         if (e == cudaSuccess) e = cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, dev);
         if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
         diag_blocks = diag_grid_blocks(num_sms);
-        // partials of the whole-lattice pass for the largest accepted lattice
-        const int nparts = std::max(diag_blocks, fused_diag_ctas(kMaxBatchN));
+        // partials of the whole-lattice pass: the most CTAs that any accepted
+        // lattice side needs (the z-chunk count of the pass depends on N, so the
+        // largest N does not give the largest grid: 1024^3 takes more CTAs
+        // than 1290^3)
+        int max_ctas = 0;
+        for (int n = 4; n <= kMaxBatchN; ++n) max_ctas = std::max(max_ctas, fused_diag_ctas(n));
+        nparts = std::max(diag_blocks, max_ctas);
         list.capacity = 1 << 20;
         if (e == cudaSuccess) e = cudaMalloc(&d_partials, sizeof(DiagPartial) * (nparts + 1));
         if (e == cudaSuccess) e = cudaMalloc(&list.count, sizeof(unsigned long long) * (1 + list.capacity));
@@ -155,7 +161,7 @@ struct Engine {
         if (e == cudaSuccess) e = cudaMalloc(&d_counter, sizeof(unsigned int));
         if (e == cudaSuccess) e = cudaMemsetAsync(d_counter, 0, sizeof(unsigned int), st);
         if (e != cudaSuccess) return e;
-        d_result = d_partials + std::max(diag_blocks, fused_diag_ctas(kMaxBatchN));
+        d_result = d_partials + nparts;
         list.items = list.count + 1;
         h_count = reinterpret_cast<unsigned long long *>(h_result + 1);
         return cudaSuccess;
@@ -273,7 +279,7 @@ struct Engine {
         const View<float> v = lat_view(L);
         const Box b{ 0, 0, 0, L.N, L.N, L.N };
         const DiagCoef dc = host_diag_coef(L.cfg, L.step);
-        cudaError_t e = launch_diag_whole<float>(v, L.N, dc, d_partials, d_result, list, diag_blocks, st);
+        cudaError_t e = launch_diag_whole<float>(v, L.N, dc, d_partials, nparts, d_result, list, diag_blocks, st);
         if (e == cudaSuccess) e = cudaMemcpyAsync(h_result, d_result, sizeof(DiagPartial), cudaMemcpyDeviceToHost, st);
         if (e == cudaSuccess)
             e = cudaMemcpyAsync(h_count, list.count, sizeof(unsigned long long), cudaMemcpyDeviceToHost, st);

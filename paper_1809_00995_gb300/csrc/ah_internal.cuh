@@ -178,10 +178,12 @@ template <typename real>
 cudaError_t launch_fused_diag(const View<real> &v, int N, const DiagArgs &da, cudaStream_t st);
 // The whole fast diagnostic: clear the list, launch_fused_diag, sum the
 // partials in a fixed order into *result, FP64 windings of the listed
-// plaquettes (fix_blocks x 128 threads).
+// plaquettes (fix_blocks x 128 threads).  partials holds `capacity` entries;
+// cudaErrorInvalidValue (nothing launched) if the N^3 pass needs more
+// (fused_diag_ctas(N), which is not monotonic in N).
 template <typename real>
 cudaError_t launch_diag_whole(const View<real> &v, int N, const DiagCoef &c, DiagPartial *partials,
-                              DiagPartial *result, DiagList list, int fix_blocks, cudaStream_t st);
+                              int capacity, DiagPartial *result, DiagList list, int fix_blocks, cudaStream_t st);
 
 // Host helpers of ah_api.cu shared with other translation units.
 KickCoef<float> host_kick_coef32(const ah_config &c, int64_t step);

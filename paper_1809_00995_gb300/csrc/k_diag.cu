@@ -404,8 +404,10 @@ int diag_grid_blocks(int num_sms) { return num_sms * 4; }
 
 template <typename real>
 cudaError_t launch_diag_whole(const View<real> &v, int N, const DiagCoef &c, DiagPartial *partials,
-                              DiagPartial *result, DiagList list, int fix_blocks, cudaStream_t st)
+                              int capacity, DiagPartial *result, DiagList list, int fix_blocks, cudaStream_t st)
 {
+    // one partial per CTA of the tile walk: refuse a buffer that cannot hold them
+    if (fused_diag_ctas(N) > capacity) return cudaErrorInvalidValue;
     cudaError_t e = cudaMemsetAsync(list.count, 0, sizeof(unsigned long long), st);
     if (e != cudaSuccess) return e;
     DiagArgs da;
@@ -418,9 +420,9 @@ cudaError_t launch_diag_whole(const View<real> &v, int N, const DiagCoef &c, Dia
     k_diag_fixup<real><<<fix_blocks, 128, 0, st>>>(v, N, list, result);
     return cudaGetLastError();
 }
-template cudaError_t launch_diag_whole<float>(const View<float> &, int, const DiagCoef &, DiagPartial *,
+template cudaError_t launch_diag_whole<float>(const View<float> &, int, const DiagCoef &, DiagPartial *, int,
                                               DiagPartial *, DiagList, int, cudaStream_t);
-template cudaError_t launch_diag_whole<double>(const View<double> &, int, const DiagCoef &, DiagPartial *,
+template cudaError_t launch_diag_whole<double>(const View<double> &, int, const DiagCoef &, DiagPartial *, int,
                                                DiagPartial *, DiagList, int, cudaStream_t);
 
 template <typename real>

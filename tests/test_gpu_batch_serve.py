@@ -104,6 +104,22 @@ def test_batch_matches_oracle_for_one_lattice():
         assert abs(go["sums"][k] - oo[name]) <= 1e-4 * abs(rho), name
 
 
+@pytest.mark.parametrize("N", [458, 512])
+def test_batch_diagnostics_of_sides_with_large_diag_grids(N):
+    """The whole-lattice diagnostics pass takes its z-chunk count from N, so many
+    sides need more CTAs (one partial each) than the largest accepted side (512^3:
+    8192, 1290^3: 6642).  A batch of such a lattice gives the single-lattice
+    observables of the same state: at step 0 exactly, after 4 steps to the FP32
+    tolerance."""
+    cfg = ah.config(N, era=ah.AH_RADIATION, s=0.0, seed=9, diag_every=0)
+    cfg.tau_end = cfg.tau0 + 4 * cfg.dt
+    series, _ = ah.ah_batch_run([cfg])
+    ref = single_series(cfg)
+    assert len(series[0]) == len(ref) == 2
+    same_obs(series[0][0], ref[0])
+    close_obs(series[0][-1], ref[-1])
+
+
 def test_batch_rejects_bad_configs():
     with pytest.raises(ah.AhError) as e:
         ah.ah_batch_run([ah.config(16, precision=ah.AH_FP64)])

@@ -23,12 +23,13 @@
  * known-answer vectors, closed-form lattice waves, exact scalar recurrences,
  * Gauss-law conservation, gauge invariance, O(dt^2) energy conservation,
  * analytic string windings, light-cone locality, the compact-theta and
- * core-growth identities); see tests/test_oracle_pins.py; the Philox
- * key/counter layout also equals cuRAND's (tests/test_gpu_curand_layout.py).
- * One part is parity unpinned: the mapping of two Philox output words to a
- * uniform double in aho_site_uniform is a convention of this code (the paper
- * draws its phases with cuRAND and gives no mapping), checked only for
- * uniformity.
+ * core-growth identities, the tension of a Bogomolny string for xi_L); see
+ * tests/test_oracle_pins.py; the Philox key/counter layout also equals
+ * cuRAND's (tests/test_gpu_curand_layout.py).  The mapping of two Philox
+ * words to a uniform double in aho_site_uniform is a convention of this code
+ * (the paper draws its phases with cuRAND and states no mapping); it is pinned
+ * to its written definition by golden values computed in exact integer
+ * arithmetic (tests/golden/make_site_uniform.py) and checked for uniformity.
  */
 #include <math.h>
 #include <stdint.h>

@@ -14,7 +14,7 @@ import numpy as np
 import pytest
 
 import oracle as O
-from inputs import coords, random_angles, random_state, straight_strings
+from inputs import bps_string, coords, random_angles, random_state, straight_strings
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
 
@@ -46,6 +46,27 @@ def test_init_random_phase_and_window_consistency():
     # distinct seeds give distinct phases
     g = O.init(O.Params(N=16, seed=6, sigma=1.3))
     assert np.mean(np.abs(g[0] - f[0]) > 1e-3) > 0.9
+
+
+def test_site_uniform_matches_its_exact_definition():
+    """The uniform behind each initial phase (Sec. 2: alpha = 2 pi u, u from
+    Philox) equals the golden values that tests/golden/make_site_uniform.py
+    computed in exact rational arithmetic from the known-answer-pinned Philox
+    words: key = seed, counter = (0, 0, index), u = (w0 2^21 + w1 >> 11) 2^-53.
+    A slip in a shift, the word order, the counter or key layout (indices and
+    seeds past 2^32 included) or the scale changes these bits."""
+    rows = [l.split() for l in open(os.path.join(GOLDEN, "site_uniform.txt"))
+            if l.strip() and not l.startswith("#")]
+    assert len(rows) >= 10
+    for seed, idx, u in rows:
+        assert O.site_uniform(int(seed), int(idx)) == float.fromhex(u), (seed, idx)
+    # the initial state uses it: phi at a site is sigma e^{2 pi i u}
+    p = O.Params(N=16, seed=1, sigma=1.0)
+    f = O.init(p)
+    u0 = float.fromhex(rows[0][2])
+    assert int(rows[0][0]) == 1 and int(rows[0][1]) == 0
+    assert abs(f[0, 0, 0, 0] - math.cos(2 * math.pi * u0)) < 1e-15
+    assert abs(f[1, 0, 0, 0] - math.sin(2 * math.pi * u0)) < 1e-15
 
 
 # ---------------------------------------------------------------- closed forms
@@ -314,6 +335,34 @@ def test_straight_string_windings(axis, N):
     o = O.observables(p, f, 0)
     assert o["sum_abs_W"] == 4 * N and o["n_pierced"] == 4 * N
     assert math.isclose(o["xi_W"], math.sqrt(N ** 3 * p.dx ** 3 / (math.pi / 6 * p.dx * 4 * N)))
+
+
+def test_bps_string_tension_fixes_xi_L():
+    """xi_L = sqrt(-mu / mean L) with mu = 2 pi sigma^2 (Eq. defXiV2; mu is the
+    tension of a string at critical coupling lambda0 = 2 e0^2).  A static straight
+    Nielsen-Olesen string, its profile solved from the Bogomolny equations with
+    scipy (inputs.bps_string), put on lattices of spacing 1/2, 1/4, 1/8 in the same
+    16^3 box: its Lagrangian per unit length must tend to -2 pi sigma^2, so that
+    xi_L tends to the box side (one string of length N dx in a volume (N dx)^3)
+    with an O(dx^2) error -- ratio 4 per halving.  This fixes mu (2 pi, not pi),
+    the square root, and the weights of K, |D phi|^2, V, E_el and the magnetic
+    term in L together (a halved magnetic coefficient misses by several per cent).
+    The string pierces exactly one xy plaquette per lattice spacing."""
+    err = []
+    for N in (32, 64, 128):
+        dx = 16.0 / N
+        f = bps_string(N, dx)
+        p = O.Params(N=N, dx=dx, dt=dx / 4, era=O.MINKOWSKI, lambda0=2.0, e0=1.0, sigma=1.0)
+        o = O.observables(p, f, 0)
+        assert o["sum_abs_W"] == N and o["n_pierced"] == N
+        assert list(o["sum_abs_W_plane"]) == [N, 0, 0]
+        mu_lat = -o["sum_L"] * dx ** 3 / (N * dx)          # tension on the lattice
+        assert abs(mu_lat / (2 * math.pi) - 1) < 0.02
+        err.append(o["xi_L"] / (N * dx) - 1.0)
+    assert 0 < err[2] < 1e-3
+    for a, b in zip(err, err[1:]):
+        assert 3.6 < a / b < 4.4, err
+    assert abs((4 * err[2] - err[1]) / 3) < 2e-5, err       # Richardson: the O(dx^2) term removed
 
 
 def test_pure_gauge_has_no_winding():

@@ -72,8 +72,10 @@ def parse():
     ap.add_argument("--variant", default=None,
                     help="step-kernel shape by name (default: autotuned), e.g. ty8_b4_w, or two_ty8_b3 "
                          "in two-step mode")
-    ap.add_argument("--serve-requests", type=int, default=40,
-                    help="requests of the serving run (500 for the full workload; 2 per second)")
+    ap.add_argument("--serve-requests", type=int, default=500,
+                    help="requests of the serving run (the full workload is 500, arriving at 2 per second)")
+    ap.add_argument("--no-batch1024", action="store_true",
+                    help="skip the batched step on one 1024^3 lattice")
     return ap.parse_args()
 
 
@@ -109,7 +111,7 @@ def peaks():
 # sources of the single-step and the two-step kernel: a traffic record is void
 # once any of its kernel's sources changes
 KERNEL_SOURCES = {"k_fused": ("k_fused.cu", "fused_common.cuh", "sincos32.cuh"),
-                  "k_fused2": ("k_fused2.cu", "fused_common.cuh", "sincos32.cuh")}
+                  "k_fused2": ("k_fused2.cu", "k_fused2_tile.cuh", "fused_common.cuh", "sincos32.cuh")}
 
 
 def kernel_source_hash(kernel):
@@ -126,19 +128,27 @@ def use_two_step(precision, diag_every, single_step=False):
     return precision == 0 and diag_every % 2 == 0 and not single_step
 
 
-def traffic_per_launch(N, kernel, variant):
-    """DRAM bytes per launch of `kernel` from the committed ncu summary, if it was
-    taken on the current kernel sources, on the shape that ran and on an N^3
-    lattice (the halo re-reads that L2 does not serve depend on the size)."""
+def traffic_record(kernel, variant):
+    """The committed ncu DRAM record of `kernel` if it was taken on the current
+    kernel sources and on the shape that ran, else None."""
     try:
         with open(TRAFFIC_FILE) as f:
             d = json.load(f)[kernel]
-        if (d.get("sources_sha256_16") != kernel_source_hash(kernel) or d.get("variant") != variant
-                or d.get("N") != N):
+        if d.get("sources_sha256_16") != kernel_source_hash(kernel) or d.get("variant") != variant:
             return None
-        return d["dram_bytes_per_site"] * N ** 3
+        return d
     except Exception:
         return None
+
+
+def traffic_per_launch(N, kernel, variant):
+    """DRAM bytes per launch of `kernel` on an N^3 lattice: the bytes per site of
+    the committed one-launch ncu capture (taken on a lattice of a few GB, see its
+    "N") times N^3.  The per-site traffic of this kernel grows little with the
+    lattice (halo re-reads that L2 no longer serves), so the scaled figure is a
+    slight underestimate on larger lattices."""
+    d = traffic_record(kernel, variant)
+    return None if d is None else d["dram_bytes_per_site"] * N ** 3
 
 
 class ClockSampler:
@@ -224,7 +234,9 @@ def batch_configs(ah, count=64, seed=4):
 
 def run_batch(ah, torch):
     cfgs = batch_configs(ah)
-    series, st = ah.ah_batch_run(cfgs, flags=ah.AH_BATCH_AUTOTUNE, series_cap=2)
+    # AH_BATCH_TWO_STEP pairs the steps of lattices of side >= 512 only: every
+    # lattice of this ensemble (N <= 256) takes one step per launch
+    series, st = ah.ah_batch_run(cfgs, flags=ah.AH_BATCH_AUTOTUNE | ah.AH_BATCH_TWO_STEP, series_cap=2)
     rate = st["site_updates"] / st["seconds"]
     # looping the single-lattice paths over a sample of the same lattices
     sample = sorted(range(len(cfgs)), key=lambda i: cfgs[i].N)[::8][:6]
@@ -248,6 +260,7 @@ def run_batch(ah, torch):
     loop_plain = loop(ah.AH_KERNEL_PLAIN)
     return {"workload": "64 FP32 lattices, N ~ U{64,96,128,192,256}, era and s uniform, seeds 100-163, "
                         "each to tau = N dx / 2; diagnostics at start and end",
+            "mode": "AH_BATCH_TWO_STEP | AH_BATCH_AUTOTUNE (every lattice here, N <= 256, one step per launch)",
             "sims_per_hour": st["sims_per_hour"], "site_updates_per_s": rate, "seconds": st["seconds"],
             "setup_seconds": st["setup_seconds"], "site_updates": st["site_updates"], "shape": st["shape"],
             "launches": st["launches"], "graph_replays": st["rounds"],
@@ -255,6 +268,29 @@ def run_batch(ah, torch):
             "speedup_vs_loop_plain": rate / loop_plain, "speedup_vs_loop_fused": rate / loop_fused,
             "loop_sample": "%d of the lattices (N = %s), each alone to its end" % (
                 len(sample), ",".join(str(cfgs[i].N) for i in sample))}
+
+
+def run_batch1024(ah, peak, flags=0, N=1024, short=40, long=100):
+    """The batched engine's step on one N^3 FP32 lattice (matter era, s = 1, seed 3):
+    two ah_batch_run jobs of `short` and `long` steps; their difference in wall
+    time over the difference in steps is the time of one batched step (setup and
+    the diagnostics at start and end cancel)."""
+    def job(n):
+        c = ah.config(N, era=ah.AH_MATTER, s=1.0, seed=3, precision=ah.AH_FP32)
+        c.tau_end = c.tau0 + n * c.dt
+        c.tau_ref = N * c.dx / 2.0
+        _, st = ah.ah_batch_run([c], flags=flags, series_cap=2)
+        return st
+    job(4)                                    # warm-up: kernels configured, pool grown
+    a, b = job(short), job(long)
+    ms = (b["seconds"] - a["seconds"]) / (long - short) * 1e3
+    gbs = 80.0 * N ** 3 / (ms / 1e3) / 1e9
+    return {"workload": "one %d^3 FP32 lattice through ah_batch_run (matter era, s = 1, seed 3)" % N,
+            "mode": "two leapfrog steps per launch" if flags & ah.AH_BATCH_TWO_STEP else "one step per launch",
+            "ms_per_step": ms, "site_updates_per_s": N ** 3 / (ms / 1e3), "alg_gbs": gbs, "peak_gbs": peak,
+            "hbm_frac": gbs / peak, "effective": bool(flags & ah.AH_BATCH_TWO_STEP),
+            "launches_per_step": (b["launches"] - a["launches"]) / (long - short),
+            "method": "difference of %d- and %d-step batch jobs (wall clock), 80 B per site-update" % (long, short)}
 
 
 def run_serve(ah, nreq, rate=2.0, seed=5, budget=150 << 30):
@@ -269,7 +305,7 @@ def run_serve(ah, nreq, rate=2.0, seed=5, budget=150 << 30):
                       s=float(rng.choice([0.0, 1.0])), seed=1000 + i, diag_every=20, precision=ah.AH_FP32)
             for i, N in enumerate(Ns)]
     ids = []
-    with ah.Server(budget, max_slots=64) as srv:
+    with ah.Server(budget, max_slots=64, flags=ah.AH_BATCH_TWO_STEP) as srv:
         t0 = time.perf_counter()
         t_next = 0.0
         for c, gap in zip(cfgs, gaps):
@@ -293,6 +329,7 @@ def run_serve(ah, nreq, rate=2.0, seed=5, budget=150 << 30):
     su = sum(c.N ** 3 * int(round((c.tau_end - c.tau0) / c.dt)) for c in cfgs)
     return {"workload": "Poisson arrivals, mean 2/s, N in {64,128,192,256,384} (weights .3/.3/.2/.15/.05), "
                         "era and s uniform, each to tau = N dx / 2, diagnostics every 20 steps, 150 GB budget",
+            "mode": "AH_BATCH_TWO_STEP (pairs for N >= 512: none in this workload, one step per launch)",
             "requests": nreq, "sims_per_hour": nreq * 3600.0 / (last - first),
             "p50_latency_s": float(np.percentile(lat, 50)), "p99_latency_s": float(np.percentile(lat, 99)),
             "mean_latency_s": float(lat.mean()), "site_updates_per_s": su / (last - first),
@@ -453,8 +490,12 @@ def main():
     achieved = alg_bytes / avg_launch_s / 1e9
     kname = "k_fused2" if two_step else "k_fused"
     tr = traffic_per_launch(N, kname, variant_name)
+    trec = traffic_record(kname, variant_name)
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": tr,
+                "traffic_source": None if trec is None else
+                "ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch at %d^3 (%.2f B/site), "
+                "scaled to %d^3 by the site count" % (trec["N"], trec["dram_bytes_per_site"], N),
                 "kernel": ("fused step, shape %s (one leapfrog step per launch)" % variant_name if not two_step else
                            "two-step fused kernel, shape %s (two leapfrog steps per launch)" % variant_name),
                 "peak_source": peak_src,
@@ -488,9 +529,12 @@ def main():
         except ah.AhError as e:
             plain = {"unavailable": str(e)}
 
-    batch = serve = None
+    batch = serve = batch1024 = None
     if rank == 0 and not a.no_batch:
         batch = run_batch(ah, torch)
+    if rank == 0 and not a.no_batch1024:
+        batch1024 = run_batch1024(ah, peak, flags=ah.AH_BATCH_TWO_STEP)
+        batch1024["one_step_per_launch"] = run_batch1024(ah, peak, flags=0)
     if rank == 0 and not a.no_serve:
         serve = run_serve(ah, a.serve_requests)
 
@@ -519,6 +563,7 @@ def main():
                              % (a.steps, diag_every)},
             "gpu_launches": a.steps * (diag_every * info["step_launches"] // steps_per_launch + 3),
             "batch": batch,
+            "batch1024": batch1024,
             "serve": serve,
             "clocks": clocks,
             "final_obs": {k: final_obs[k] for k in ("step", "tau", "xi_L", "xi_W", "v2_V", "v2_L", "v2_omega",

@@ -254,32 +254,65 @@ ah_status ah_autotune(ah_sim *sim, int32_t trial_steps, int32_t *chosen);
  * step counter on the device; the steps between diagnostic points are replayed
  * from a CUDA graph.  Every lattice computes exactly what ah_step computes for
  * it alone. */
-enum { AH_BATCH_AUTOTUNE = 1, AH_BATCH_NO_GRAPH = 2 };
+/* Steps in pairs.  A lattice whose configuration has AH_FLAG_TWO_STEP, and,
+ * with the batch (or server) flag AH_BATCH_TWO_STEP, every lattice of side
+ * N >= 512, is advanced two steps per launch by the batched two-step pass
+ * (temporal blocking, as AH_FLAG_TWO_STEP does for one simulation: the state
+ * is read and written once per two steps), and by a single step only when one
+ * step is left before its next diagnostic point or its end, so the grouping of
+ * its steps, and its results, do not depend on the other lattices of the
+ * batch.  Such a lattice holds a second Pi/E set (20 instead of 15 arrays of
+ * N^3 floats).  Its results agree with one step per launch to FP32 rounding.
+ * The other lattices take one step per launch.  (Small lattices gain nothing
+ * from pairs: the two-step tile writes 30 x 6 of its 32 x 8 sites.) */
+enum { AH_BATCH_AUTOTUNE = 1, AH_BATCH_NO_GRAPH = 2, AH_BATCH_TWO_STEP = 4 };
 
 typedef struct ah_batch_stats {
     double seconds;          /* wall time of the evolution and diagnostics       */
     double setup_seconds;    /* allocation, initial states, shape tuning         */
     double site_updates;     /* sum over lattices of N^3 x steps                 */
     double sims_per_hour;    /* count x 3600 / seconds                           */
-    int32_t shape;           /* batched-kernel shape used                        */
+    int32_t shape;           /* batched-kernel shape used (the two-step pass's
+                                shape with AH_BATCH_TWO_STEP)                    */
     int32_t rounds;          /* graph (or launch-sequence) replays               */
     int64_t launches;        /* kernel launches of the batched steps             */
 } ah_batch_stats;
 
-/* Run `count` lattices (cfgs[i]: precision AH_FP32; each runs
+/* Run `count` lattices (cfgs[i]: precision AH_FP32, N <= 1290; each runs
  * round((tau_end - tau0)/dt) steps) to their ends.  If series is not NULL it
  * holds count x series_cap ah_obs (lattice-major): for lattice i, observables at
  * step 0, every cfgs[i].diag_every steps (if > 0) and at the end;
  * series_len[i] receives the number produced (entries past series_cap are
  * dropped).  flags: AH_BATCH_AUTOTUNE (time each batched shape on the initial
- * states, then restore them), AH_BATCH_NO_GRAPH (plain launches).  stats may be
- * NULL.  Synchronous; all device memory is released before return.  Of the
- * per-lattice cfgs[i].flags, AH_FLAG_WRAP_THETA and AH_FLAG_CORE_GROWTH apply;
- * AH_FLAG_AUTOTUNE, AH_FLAG_EXACT_DIAG and AH_FLAG_TWO_STEP have no effect (the
- * batched kernel advances one step per launch, and the diagnostics are those of
- * the whole-lattice pass).  The same holds for requests to the server. */
+ * states, then restore them), AH_BATCH_NO_GRAPH (plain launches),
+ * AH_BATCH_TWO_STEP (lattices of side >= 512 in pairs, see above).  stats may
+ * be NULL.  Synchronous; all device memory is released before return.  Of the
+ * per-lattice cfgs[i].flags, AH_FLAG_WRAP_THETA, AH_FLAG_CORE_GROWTH and
+ * AH_FLAG_TWO_STEP (steps in pairs) apply; AH_FLAG_AUTOTUNE and
+ * AH_FLAG_EXACT_DIAG have no effect (the diagnostics are those of the
+ * whole-lattice pass).  The same holds for requests to the server. */
 ah_status ah_batch_run(const ah_config *cfgs, int32_t count, int32_t flags, ah_obs *series,
                        int64_t series_cap, int64_t *series_len, ah_batch_stats *stats);
+
+/* A window of a lattice's final state to copy to host memory: the sites
+ * [x0, x0+nx) x [y0, y0+ny) x [z0, z0+nz) taken mod N (1 <= nx, ny, nz <= N),
+ * written to `out` as FP64 in the layout of ah_get_fields (10 components of
+ * nz*ny*nx values, x fastest).  `out` is caller-owned host memory. */
+typedef struct ah_window {
+    int32_t lattice;              /* ah_batch_run_ex: index into cfgs; ignored by the server */
+    int32_t x0, y0, z0, nx, ny, nz;
+    double *out;
+} ah_window;
+
+/* ah_batch_run, plus field read-back: after every lattice has reached its end,
+ * each of the `nwindows` windows (any number per lattice) receives its
+ * lattice's final state (phi^n, theta^n, Pi^{n-1/2}, E^{n-1/2} at its last step
+ * n, the state the last entry of its series describes).  AH_ERR_ARG for a
+ * window whose lattice index or extent is out of range or whose buffer is
+ * NULL (checked before any work). */
+ah_status ah_batch_run_ex(const ah_config *cfgs, int32_t count, int32_t flags, ah_obs *series,
+                          int64_t series_cap, int64_t *series_len, ah_batch_stats *stats,
+                          const ah_window *windows, int32_t nwindows);
 
 /* ---- continuous-batching server ----
  *
@@ -298,10 +331,20 @@ typedef struct ah_server_stats {
     int64_t launches;        /* kernel launches of the batched steps             */
 } ah_server_stats;
 
-/* Start a server on the current device.  flags: 0 or AH_BATCH_NO_GRAPH. */
+/* Start a server on the current device.  flags: AH_BATCH_NO_GRAPH,
+ * AH_BATCH_TWO_STEP (requests of side >= 512 in pairs; a request stepped in
+ * pairs takes 20 instead of 15 arrays of N^3 floats of the budget). */
 ah_status ah_server_create(size_t hbm_budget_bytes, int32_t max_slots, int32_t flags, ah_server **out);
-/* Queue one run (precision AH_FP32); AH_ERR_OOM if it can never fit the budget. */
+/* Queue one run (precision AH_FP32, N <= 1290); AH_ERR_OOM if it can never fit
+ * the budget. */
 ah_status ah_server_submit(ah_server *srv, const ah_config *cfg, uint64_t *req_id);
+/* The same, plus windows of the run's final state (ah_window; `lattice` is
+ * ignored) written when the run completes, before ah_server_poll reports it
+ * done.  The buffers must stay valid until ah_server_poll returns AH_OK,
+ * AH_ERR_CANCELLED or AH_ERR_CUDA for this request (a cancelled or failed run
+ * may leave them unwritten). */
+ah_status ah_server_submit_ex(ah_server *srv, const ah_config *cfg, const ah_window *windows,
+                              int32_t nwindows, uint64_t *req_id);
 /* AH_OK with the final observables and times once done; AH_ERR_BUSY while queued
  * or running; AH_ERR_CANCELLED, AH_ERR_NOTFOUND, AH_ERR_CUDA (failed run). */
 ah_status ah_server_poll(ah_server *srv, uint64_t req_id, ah_obs *final_out, double *t_submit,

@@ -27,7 +27,7 @@ AH_MINKOWSKI, AH_RADIATION, AH_MATTER = 0, 1, 2
 AH_FP32, AH_FP64 = 0, 1
 AH_KERNEL_AUTO, AH_KERNEL_PLAIN, AH_KERNEL_FUSED = 0, 1, 2
 AH_FLAG_EXACT_DIAG, AH_FLAG_AUTOTUNE, AH_FLAG_WRAP_THETA, AH_FLAG_CORE_GROWTH, AH_FLAG_TWO_STEP = 1, 2, 4, 8, 16
-AH_BATCH_AUTOTUNE, AH_BATCH_NO_GRAPH = 1, 2
+AH_BATCH_AUTOTUNE, AH_BATCH_NO_GRAPH, AH_BATCH_TWO_STEP = 1, 2, 4
 
 SUM_NAMES = ("L", "rho", "p", "K", "G2", "V", "Eel", "B", "KV", "G2V", "KL", "G2L", "pL", "rhoL",
              "gauss2", "gscale2")
@@ -74,6 +74,12 @@ class ah_batch_stats(ctypes.Structure):
                 ("launches", ctypes.c_int64)]
 
 
+class ah_window(ctypes.Structure):
+    _fields_ = [("lattice", ctypes.c_int32), ("x0", ctypes.c_int32), ("y0", ctypes.c_int32), ("z0", ctypes.c_int32),
+                ("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("nz", ctypes.c_int32),
+                ("out", ctypes.c_void_p)]
+
+
 class ah_server_stats(ctypes.Structure):
     _fields_ = [("submitted", ctypes.c_int64), ("admitted", ctypes.c_int64), ("completed", ctypes.c_int64),
                 ("running", ctypes.c_int32), ("queued", ctypes.c_int32), ("hbm_used", ctypes.c_int64),
@@ -112,6 +118,11 @@ _SIGS = {
                                 ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p], ctypes.c_int),
     "ah_batch_run": ([ctypes.POINTER(ah_config), ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(ah_obs),
                       ctypes.c_int64, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ah_batch_stats)], ctypes.c_int),
+    "ah_batch_run_ex": ([ctypes.POINTER(ah_config), ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(ah_obs),
+                         ctypes.c_int64, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ah_batch_stats),
+                         ctypes.POINTER(ah_window), ctypes.c_int32], ctypes.c_int),
+    "ah_server_submit_ex": ([ctypes.c_void_p, ctypes.POINTER(ah_config), ctypes.POINTER(ah_window), ctypes.c_int32,
+                             ctypes.POINTER(ctypes.c_uint64)], ctypes.c_int),
     "ah_server_create": ([ctypes.c_size_t, ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(ctypes.c_void_p)],
                          ctypes.c_int),
     "ah_server_submit": ([ctypes.c_void_p, ctypes.POINTER(ah_config), ctypes.POINTER(ctypes.c_uint64)], ctypes.c_int),
@@ -269,6 +280,20 @@ def ah_observables_noalloc(field_ptrs, N: int, cfg: ah_config, step: int, d_sums
     _check(load().ah_observables_noalloc(arr, N, ctypes.byref(cfg), step, d_sums_ptr, stream_ptr or None))
 
 
+def _windows(wins, lattice_of=None):
+    """ah_window array and the numpy buffers it points to, from (x0, y0, z0, nx, ny, nz)
+    boxes (with a leading lattice index when lattice_of is None)."""
+    arr = (ah_window * max(1, len(wins)))()
+    bufs = []
+    for k, w in enumerate(wins):
+        lat, box = (w[0], w[1:]) if lattice_of is None else (lattice_of, w)
+        x0, y0, z0, nx, ny, nz = box
+        b = np.empty((10, nz, ny, nx), dtype=np.float64)
+        bufs.append(b)
+        arr[k] = ah_window(lat, x0, y0, z0, nx, ny, nz, b.ctypes.data)
+    return arr, bufs
+
+
 def ah_batch_run(cfgs, flags: int = 0, series_cap: int = 64):
     """Run a batch of FP32 lattices to their ends; returns (series, stats): series[i]
     is the list of observable dicts of lattice i (step 0, every diag_every, end)."""
@@ -282,6 +307,21 @@ def ah_batch_run(cfgs, flags: int = 0, series_cap: int = 64):
     return out, {k: getattr(st, k) for k, _ in st._fields_}
 
 
+def ah_batch_run_ex(cfgs, windows=(), flags: int = 0, series_cap: int = 64):
+    """ah_batch_run plus read-back of final-state windows: `windows` holds
+    (lattice, x0, y0, z0, nx, ny, nz) tuples; returns (series, stats, fields) with
+    fields[k] the (10, nz, ny, nx) FP64 array of window k."""
+    n = len(cfgs)
+    arr = (ah_config * n)(*cfgs)
+    series = (ah_obs * (n * series_cap))()
+    lens = (ctypes.c_int64 * n)()
+    st = ah_batch_stats()
+    warr, bufs = _windows(list(windows))
+    _check(load().ah_batch_run_ex(arr, n, flags, series, series_cap, lens, ctypes.byref(st), warr, len(bufs)))
+    out = [[series[i * series_cap + k].as_dict() for k in range(min(lens[i], series_cap))] for i in range(n)]
+    return out, {k: getattr(st, k) for k, _ in st._fields_}, bufs
+
+
 class Server:
     """Continuous-batching server (ah_server_*): submit runs, poll their results."""
 
@@ -289,11 +329,22 @@ class Server:
         h = ctypes.c_void_p()
         _check(load().ah_server_create(hbm_budget_bytes, max_slots, flags, ctypes.byref(h)))
         self.h = h.value
+        self._keep = {}
 
     def submit(self, cfg: ah_config) -> int:
         rid = ctypes.c_uint64()
         _check(load().ah_server_submit(self.h, ctypes.byref(cfg), ctypes.byref(rid)))
         return rid.value
+
+    def submit_ex(self, cfg: ah_config, windows=()):
+        """Queue a run whose final-state windows ((x0, y0, z0, nx, ny, nz) boxes) are
+        written when it completes; returns (request id, list of (10, nz, ny, nx)
+        arrays), valid once poll() reports the request done."""
+        rid = ctypes.c_uint64()
+        warr, bufs = _windows(list(windows), lattice_of=0)
+        _check(load().ah_server_submit_ex(self.h, ctypes.byref(cfg), warr, len(bufs), ctypes.byref(rid)))
+        self._keep[rid.value] = (warr, bufs)      # the library writes into these buffers later
+        return rid.value, bufs
 
     def poll(self, rid: int):
         """None while queued or running, else (obs dict, t_submit, t_done)."""
@@ -316,6 +367,7 @@ class Server:
         if self.h:
             load().ah_server_destroy(self.h)
             self.h = None
+            self._keep = {}
 
     def __enter__(self):
         return self

@@ -9,6 +9,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 #include <map>
@@ -138,6 +139,8 @@ struct ah_sim {
     TmaMaps tmaps[2];  // per read buffer (phi/theta ping-pong index)
     int *d_err;        // device error word of the bounded waits
     int *host_err;
+    long long tma_wait_limit;   // clock cycles per bounded wait of the TMA-fed step
+    int tma_drop_q;             // fault injection: Pi/E plane whose copy is never issued (-1: none)
     cudaStream_t stream;
     bool own_stream;
 };
@@ -279,7 +282,7 @@ ah_status do_step(ah_sim *h, int64_t n)
             } else {
                 const TmaShape &t = kTmaShapes[idx];
                 AH_CUDA(launch_fused_tma(h->tmaps[h->cur], make_view(F, h->cur, true), h->N, k, h->d_err, t.minb,
-                                         t.min_chunk, h->stream));
+                                         t.min_chunk, h->tma_wait_limit, h->tma_drop_q, h->stream));
             }
             h->cur ^= 1;
         }
@@ -337,6 +340,9 @@ ah_status do_diag(ah_sim *h, Box b, ah_obs *out)
     const View<real> v = make_view(F, h->cur, false);
     const bool exact = (h->cfg.flags & AH_FLAG_EXACT_DIAG) != 0;
     const bool whole = b.x0 == 0 && b.y0 == 0 && b.z0 == 0 && b.nx == h->N && b.ny == h->N && b.nz == h->N;
+    if (whole && !exact && fused_diag_ctas(h->N) > h->nparts)
+        return fail(AH_ERR_CUDA, "diagnostics scratch too small: the N=%d pass needs %d partials, %d allocated",
+                    h->N, fused_diag_ctas(h->N), h->nparts);
     if (whole && !exact)
         AH_CUDA(launch_diag_whole<real>(v, h->N, dc, h->partials, h->nparts, h->result, h->list, h->diag_blocks,
                                         h->stream));
@@ -439,8 +445,8 @@ ah_status enter(const ah_sim *h)
 
 namespace ah {
 KickCoef<float> host_kick_coef32(const ah_config &c, int64_t step) { return kick_coef<float>(c, step); }
-void host_carve32(Fields<float> &F, void *base, size_t nsites) { carve(F, (char *)base, nsites); }
-size_t host_state_bytes32(size_t nsites) { return 15 * padded(nsites) * sizeof(float); }
+void host_carve32(Fields<float> &F, void *base, size_t nsites, bool spare) { carve(F, (char *)base, nsites, spare); }
+size_t host_state_bytes32(size_t nsites, bool spare) { return (spare ? 20 : 15) * padded(nsites) * sizeof(float); }
 void host_fill_obs(const ah_config &c, int64_t step, int64_t n_sites, const DiagPartial &r, ah_obs *out)
 {
     fill_obs(c, step, n_sites, r, out);
@@ -453,7 +459,7 @@ ah_status host_fail(ah_status st, const char *msg) { return fail(st, "%s", msg);
 
 extern "C" {
 
-int ah_abi_version(void) { return 2; }
+int ah_abi_version(void) { return 3; }
 
 const char *ah_last_error(void) { return g_err.c_str(); }
 
@@ -492,6 +498,14 @@ ah_status ah_create_ex(const ah_config *cfg, ah_sim **out)
     h->variant = cfg->precision == AH_FP32 ? fused_default_variant<float>() : fused_default_variant<double>();
     h->two_step = (cfg->flags & AH_FLAG_TWO_STEP) != 0;
     h->variant2 = fused2_default_variant();
+    // fault injection for tests, read at creation: AH_TMA_DROP_COPY=q makes the
+    // TMA-fed step leave the copy of Pi/E plane q of every CTA unissued, so that
+    // the bounded wait for it gives up (AH_ERR_TIMEOUT from ah_sync);
+    // AH_TMA_WAIT_LIMIT_CYCLES shortens that bound
+    h->tma_wait_limit = kTmaWaitLimit;
+    h->tma_drop_q = -1;
+    if (const char *w = std::getenv("AH_TMA_WAIT_LIMIT_CYCLES")) h->tma_wait_limit = std::max(0LL, std::atoll(w));
+    if (const char *q = std::getenv("AH_TMA_DROP_COPY")) h->tma_drop_q = std::max(-1, std::atoi(q));
     h->nsites = (long long)cfg->N * cfg->N * cfg->N;
     h->step = 0;
     h->cur = 0;

@@ -5,7 +5,10 @@
 // fused step of k_fused.cu: one persistent launch per step advances every
 // resident lattice, whatever its size, by one leapfrog step (Eqs. up_pi, up_E,
 // up_phi, up_A), each with its own coefficient table and step counter in device
-// memory.  Steps between diagnostic points are replayed from a CUDA graph.
+// memory.  With AH_BATCH_TWO_STEP the batched two-step pass of k_fused2.cu
+// advances every lattice by two steps per launch (temporal blocking; a round
+// with an odd number of steps ends with one single-step launch).  Steps
+// between diagnostic points are replayed from a CUDA graph.
 //
 //  * ah_batch_run: a fixed set of lattices, each run to its own tau_end, with
 //    diagnostics at step 0, every diag_every steps and at the end.
@@ -16,6 +19,7 @@
 #include <algorithm>
 #include <chrono>
 #include <condition_variable>
+#include <cstdio>
 #include <cstdlib>
 #include <cstring>
 #include <deque>
@@ -37,6 +41,13 @@ using namespace ah;
 namespace {
 
 constexpr int kZChunk = 64;        // planes per work item
+constexpr int kZChunk2 = 256;      // planes per two-step work item (each also runs two extra planes)
+// Two-step batches step the lattices of at least this side in pairs and the
+// smaller ones one step per launch: the two-step tile writes 30 x 6 of its
+// 32 x 8 sites, so small lattices pay more in partial tiles and halo
+// recomputation than they save in DRAM traffic (on GB300 two-step passes tie
+// single steps at 512^3 and win at 1024^3).
+constexpr int kPairMinN = 512;
 constexpr int kServerRound = 20;   // longest round of the server (admission latency bound)
 constexpr int kMaxBatchN = 1290;   // largest lattice side with 32-bit site indices (1290^3 < 2^31)
 
@@ -53,7 +64,8 @@ struct Lat {
     ah_config cfg;
     int N = 0;
     long long nsites = 0;
-    int nsteps = 0, step = 0, cur = 0;
+    int nsteps = 0, step = 0, cur = 0, pe = 0;
+    bool two = false;                 // stepped in pairs (second Pi/E set for the two-step pass)
     void *mem = nullptr;
     size_t bytes = 0;
     Fields<float> F{};
@@ -61,34 +73,45 @@ struct Lat {
     // server bookkeeping
     uint64_t id = 0;
     double t_submit = 0.0;
+    std::vector<ah_window> wins;      // windows written when the request completes
 };
 
-size_t lattice_bytes(const ah_config &c)
+// A lattice is stepped in pairs if its configuration asks for it
+// (AH_FLAG_TWO_STEP) or, with auto_pairs (AH_BATCH_TWO_STEP), if N >= kPairMinN.
+bool lat_pairs(const ah_config &c, bool auto_pairs)
+{
+    return (c.flags & AH_FLAG_TWO_STEP) || (auto_pairs && c.N >= kPairMinN);
+}
+
+size_t lattice_bytes(const ah_config &c, bool two)
 {
     const size_t n = (size_t)c.N * c.N * c.N;
-    return align256(host_state_bytes32(n)) + align256(sizeof(KickCoef<float>) * (size_t)host_run_steps(c));
+    return align256(host_state_bytes32(n, two)) + align256(sizeof(KickCoef<float>) * (size_t)host_run_steps(c));
 }
 
 // Allocate (stream-ordered), write the random-phase state and the coefficient table.
-cudaError_t lat_setup(Lat &L, cudaStream_t st)
+cudaError_t lat_setup(Lat &L, bool two, cudaStream_t st)
 {
     L.N = L.cfg.N;
     L.nsites = (long long)L.N * L.N * L.N;
     L.nsteps = (int)host_run_steps(L.cfg);
     L.step = 0;
     L.cur = 0;
-    L.bytes = lattice_bytes(L.cfg);
+    L.pe = 0;
+    L.two = two;
+    L.bytes = lattice_bytes(L.cfg, two);
     cudaError_t e = cudaMallocAsync(&L.mem, L.bytes, st);
     if (e != cudaSuccess) {
         L.mem = nullptr;
         cudaGetLastError();                  // clear the refused allocation's error
         return e;
     }
-    host_carve32(L.F, L.mem, (size_t)L.nsites);
-    L.coefs = reinterpret_cast<KickCoef<float> *>(static_cast<char *>(L.mem) + align256(host_state_bytes32(L.nsites)));
+    const size_t sb = host_state_bytes32(L.nsites, two);
+    host_carve32(L.F, L.mem, (size_t)L.nsites, two);
+    L.coefs = reinterpret_cast<KickCoef<float> *>(static_cast<char *>(L.mem) + align256(sb));
     std::vector<KickCoef<float>> tab(std::max(1, L.nsteps));
     for (int n = 0; n < L.nsteps; ++n) tab[n] = host_kick_coef32(L.cfg, n);
-    e = cudaMemsetAsync(L.mem, 0, host_state_bytes32(L.nsites), st);
+    e = cudaMemsetAsync(L.mem, 0, sb, st);
     if (e == cudaSuccess) e = launch_init_phase<float>(L.F.phr[0], L.F.phi[0], L.N, L.cfg.seed, L.cfg.sigma, st);
     if (e == cudaSuccess && L.nsteps > 0)
         e = cudaMemcpyAsync(L.coefs, tab.data(), sizeof(KickCoef<float>) * L.nsteps, cudaMemcpyHostToDevice, st);
@@ -100,47 +123,72 @@ cudaError_t lat_reinit(Lat &L, cudaStream_t st)
 {
     L.step = 0;
     L.cur = 0;
-    cudaError_t e = cudaMemsetAsync(L.mem, 0, host_state_bytes32(L.nsites), st);
+    L.pe = 0;
+    cudaError_t e = cudaMemsetAsync(L.mem, 0, host_state_bytes32(L.nsites, L.two), st);
     if (e == cudaSuccess) e = launch_init_phase<float>(L.F.phr[0], L.F.phi[0], L.N, L.cfg.seed, L.cfg.sigma, st);
     return e;
 }
 
+// The lattice's buffers with Pi and E of its current set in F.pir, F.pii, F.el.
+Fields<float> lat_fields(const Lat &L)
+{
+    Fields<float> F = L.F;
+    if (L.pe) {
+        F.pir = L.F.spare[0];
+        F.pii = L.F.spare[1];
+        for (int d = 0; d < 3; ++d) F.el[d] = L.F.spare[2 + d];
+    }
+    return F;
+}
+
 View<float> lat_view(const Lat &L)
 {
+    const Fields<float> F = lat_fields(L);
     View<float> v{};
     const int c = L.cur;
-    v.phr = L.F.phr[c]; v.phi = L.F.phi[c];
-    v.th1 = L.F.th[c][0]; v.th2 = L.F.th[c][1]; v.th3 = L.F.th[c][2];
-    v.pir = L.F.pir; v.pii = L.F.pii;
-    v.e1 = L.F.el[0]; v.e2 = L.F.el[1]; v.e3 = L.F.el[2];
+    v.phr = F.phr[c]; v.phi = F.phi[c];
+    v.th1 = F.th[c][0]; v.th2 = F.th[c][1]; v.th3 = F.th[c][2];
+    v.pir = F.pir; v.pii = F.pii;
+    v.e1 = F.el[0]; v.e2 = F.el[1]; v.e3 = F.el[2];
     return v;
+}
+
+ah_status check_window(const ah_window &w, int N)
+{
+    if (!w.out) return host_fail(AH_ERR_ARG, "window with a null output buffer");
+    if (w.nx < 1 || w.ny < 1 || w.nz < 1 || w.nx > N || w.ny > N || w.nz > N)
+        return host_fail(AH_ERR_ARG, "window extent must be in [1, N]");
+    return AH_OK;
 }
 
 // Device tables and scratch of one batched run (grown on demand).
 struct Engine {
     cudaStream_t st = nullptr;
     int num_sms = 0, shape = 0;
+    bool two = false;                  // the batch may hold lattices stepped in pairs
+    int shape2 = 0;                    // shape of the batched two-step pass
     BatchLattice *d_lat = nullptr;
     BatchState *d_state = nullptr;
-    int2 *d_items = nullptr;
-    int *d_nitems = nullptr;
+    int2 *d_items = nullptr, *d_items2 = nullptr;
+    int *d_nitems = nullptr;           // [0] single-step items, [1] two-step items
     unsigned int *d_counter = nullptr;
     int cap_lat = 0;
-    long long cap_items = 0;
+    long long cap_items = 0, cap_items2 = 0;
     DiagPartial *d_partials = nullptr, *d_result = nullptr, *h_result = nullptr;
     int nparts = 0;                    // entries of d_partials before d_result
     DiagList list{};
     unsigned long long *h_count = nullptr;
     int diag_blocks = 0;
-    // (shape, R, lattices loaded) -> R batched steps
+    // (shape key, R, lattices loaded) -> R batched steps
     std::map<std::tuple<int, int, int>, cudaGraphExec_t> graphs;
     bool use_graph = true;
     long long launches = 0;
     int rounds = 0;
 
-    cudaError_t init(bool graph)
+    cudaError_t init(bool graph, bool two_step)
     {
         use_graph = graph;
+        two = two_step;
         int dev = 0;
         cudaError_t e = cudaGetDevice(&dev);
         if (e == cudaSuccess) e = cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, dev);
@@ -157,7 +205,7 @@ struct Engine {
         if (e == cudaSuccess) e = cudaMalloc(&d_partials, sizeof(DiagPartial) * (nparts + 1));
         if (e == cudaSuccess) e = cudaMalloc(&list.count, sizeof(unsigned long long) * (1 + list.capacity));
         if (e == cudaSuccess) e = cudaMallocHost(&h_result, sizeof(DiagPartial) + 64);
-        if (e == cudaSuccess) e = cudaMalloc(&d_nitems, sizeof(int));
+        if (e == cudaSuccess) e = cudaMalloc(&d_nitems, 2 * sizeof(int));
         if (e == cudaSuccess) e = cudaMalloc(&d_counter, sizeof(unsigned int));
         if (e == cudaSuccess) e = cudaMemsetAsync(d_counter, 0, sizeof(unsigned int), st);
         if (e != cudaSuccess) return e;
@@ -177,7 +225,7 @@ struct Engine {
     {
         if (st) cudaStreamSynchronize(st);
         clear_graphs();
-        cudaFree(d_lat); cudaFree(d_state); cudaFree(d_items);
+        cudaFree(d_lat); cudaFree(d_state); cudaFree(d_items); cudaFree(d_items2);
         cudaFree(d_nitems); cudaFree(d_counter); cudaFree(d_partials);
         if (list.count) cudaFree(list.count);
         if (h_result) cudaFreeHost(h_result);
@@ -191,26 +239,42 @@ struct Engine {
         const int n = (int)lats.size();
         std::vector<BatchLattice> bl(n);
         std::vector<BatchState> bs(n);
-        std::vector<int2> items;
+        std::vector<int2> items, items2;
         std::vector<int> order(n);
         for (int i = 0; i < n; ++i) order[i] = i;
         std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return lats[a]->N > lats[b]->N; });
         for (int i = 0; i < n; ++i) {
             const Lat &L = *lats[i];
             BatchLattice &B = bl[i];
+            memset(&B, 0, sizeof B);
             B.F = L.F;
+            float *const q0[5] = { L.F.pir, L.F.pii, L.F.el[0], L.F.el[1], L.F.el[2] };
+            for (int k = 0; k < 5; ++k) {
+                B.q[0][k] = q0[k];
+                B.q[1][k] = L.F.spare[k];
+            }
             B.N = L.N;
             batch_tiles(shape, L.N, &B.tiles_x, &B.tiles_y);
             B.zc = std::min(L.N, kZChunk);
             B.nchunk = (L.N + B.zc - 1) / B.zc;
+            if (two && L.two) {
+                B.pairs = 1;
+                batch2_tiles(shape2, L.N, &B.tiles2_x, &B.tiles2_y);
+                B.zc2 = std::min(L.N, kZChunk2);
+                B.nchunk2 = (L.N + B.zc2 - 1) / B.zc2;
+            }
             B.nsteps = L.nsteps;
+            B.diag_every = L.cfg.diag_every;
             B.coefs = L.coefs;
             bs[i].step = L.step;
             bs[i].cur = L.cur;
+            bs[i].pe = L.pe;
         }
         for (int i : order) {
             const int cnt = bl[i].tiles_x * bl[i].tiles_y * bl[i].nchunk;
             for (int k = 0; k < cnt; ++k) items.push_back(make_int2(i, k));
+            const int cnt2 = bl[i].tiles2_x * bl[i].tiles2_y * bl[i].nchunk2;
+            for (int k = 0; k < cnt2; ++k) items2.push_back(make_int2(i, k));
         }
         cudaError_t e = cudaSuccess;
         if (n > cap_lat) {
@@ -226,14 +290,64 @@ struct Engine {
             e = cudaMalloc(&d_items, sizeof(int2) * cap_items);
             clear_graphs();
         }
-        const int ni = (int)items.size();
+        if (e == cudaSuccess && (long long)items2.size() > cap_items2) {
+            cudaFree(d_items2);
+            cap_items2 = std::max<long long>((long long)items2.size(), 2 * cap_items2);
+            e = cudaMalloc(&d_items2, sizeof(int2) * cap_items2);
+            clear_graphs();
+        }
+        const int ni[2] = { (int)items.size(), (int)items2.size() };
         if (e == cudaSuccess && n) e = cudaMemcpyAsync(d_lat, bl.data(), sizeof(BatchLattice) * n, cudaMemcpyHostToDevice, st);
         if (e == cudaSuccess && n) e = cudaMemcpyAsync(d_state, bs.data(), sizeof(BatchState) * n, cudaMemcpyHostToDevice, st);
-        if (e == cudaSuccess && ni) e = cudaMemcpyAsync(d_items, items.data(), sizeof(int2) * ni, cudaMemcpyHostToDevice, st);
-        if (e == cudaSuccess) e = cudaMemcpyAsync(d_nitems, &ni, sizeof(int), cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess && ni[0])
+            e = cudaMemcpyAsync(d_items, items.data(), sizeof(int2) * ni[0], cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess && ni[1])
+            e = cudaMemcpyAsync(d_items2, items2.data(), sizeof(int2) * ni[1], cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(d_nitems, ni, 2 * sizeof(int), cudaMemcpyHostToDevice, st);
         if (e == cudaSuccess) e = cudaStreamSynchronize(st);   // host vectors above
         nlat_loaded = n;
+        n_paired = n_unpaired = 0;
+        for (int i = 0; i < n; ++i) (bl[i].pairs ? n_paired : n_unpaired) += 1;
         return e;
+    }
+    int n_paired = 0, n_unpaired = 0;   // loaded lattices stepped in pairs / one step at a time
+
+    // The launches of a round of R batched steps (R: the fewest steps any
+    // unfinished lattice has to its next stop).  One step per launch: R
+    // launches.  Two-step mode: R / 2 times a two-step pass of the paired
+    // lattices and two single steps of the others, then for an odd R one single
+    // step of the others and of the paired lattices one step before their next
+    // stop (the paired lattices keep their steps in pairs, see batch_stop).
+    cudaError_t enqueue_steps(int R)
+    {
+        if (two) {
+            auto single = [&](int mode) {
+                launches += 2;
+                return launch_fused_batch(shape, d_lat, d_state, nlat_loaded, d_items, d_nitems, d_counter, num_sms, st,
+                                          mode);
+            };
+            for (int r = 0; r < R / 2; ++r) {
+                if (n_paired) {
+                    cudaError_t e = launch_fused2_batch(shape2, d_lat, d_state, nlat_loaded, d_items2, d_nitems + 1,
+                                                        d_counter, num_sms, st);
+                    if (e != cudaSuccess) return e;
+                    launches += 2;
+                }
+                for (int k = 0; k < 2 && n_unpaired; ++k) {
+                    cudaError_t e = single(BATCH_UNPAIRED);
+                    if (e != cudaSuccess) return e;
+                }
+            }
+            if (R % 2) return single(BATCH_ROUND_END);
+            return cudaSuccess;
+        }
+        for (int r = 0; r < R; ++r) {
+            cudaError_t e = launch_fused_batch(shape, d_lat, d_state, nlat_loaded, d_items, d_nitems, d_counter,
+                                               num_sms, st);
+            if (e != cudaSuccess) return e;
+            launches += 2;
+        }
+        return cudaSuccess;
     }
     int nlat_loaded = 0;
 
@@ -242,23 +356,16 @@ struct Engine {
     {
         TraceRange tr("batch steps");
         if (R <= 0) return cudaSuccess;
-        launches += 2LL * R;
         ++rounds;
-        if (!use_graph) {
-            for (int r = 0; r < R; ++r) {
-                cudaError_t e = launch_fused_batch(shape, d_lat, d_state, nlat_loaded, d_items, d_nitems, d_counter,
-                                                   num_sms, st);
-                if (e != cudaSuccess) return e;
-            }
-            return cudaSuccess;
-        }
-        const auto key = std::make_tuple(shape, R, nlat_loaded);
+        if (!use_graph) return enqueue_steps(R);
+        const long long before = launches;
+        const int mix = (n_paired ? 1 : 0) + (n_unpaired ? 2 : 0);
+        const auto key = std::make_tuple(two ? 1000 + 64 * mix + 16 * shape2 + shape : shape, R, nlat_loaded);
         auto it = graphs.find(key);
         if (it == graphs.end()) {
             cudaGraph_t g;
             cudaError_t e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
-            for (int r = 0; r < R && e == cudaSuccess; ++r)
-                e = launch_fused_batch(shape, d_lat, d_state, nlat_loaded, d_items, d_nitems, d_counter, num_sms, st);
+            if (e == cudaSuccess) e = enqueue_steps(R);
             cudaError_t e2 = cudaStreamEndCapture(st, &g);
             if (e != cudaSuccess) return e;
             if (e2 != cudaSuccess) return e2;
@@ -267,8 +374,40 @@ struct Engine {
             cudaGraphDestroy(g);
             if (e != cudaSuccess) return e;
             it = graphs.emplace(key, ex).first;
+            launches = before;
         }
+        launches = before + (two ? 2LL * ((R / 2) * ((n_paired ? 1 : 0) + (n_unpaired ? 2 : 0)) + R % 2)
+                                 : 2LL * R);
         return cudaGraphLaunch(it->second, st);
+    }
+
+    // Copy window w of lattice L's current state to w.out (host, FP64).
+    ah_status gather(const Lat &L, const ah_window &w)
+    {
+        const int N = L.N;
+        auto md = [N](int v) { v %= N; return v < 0 ? v + N : v; };
+        const Box b{ md(w.x0), md(w.y0), md(w.z0), w.nx, w.ny, w.nz };
+        const size_t bytes = sizeof(double) * 10 * (size_t)w.nx * w.ny * w.nz;
+        double *tmp = nullptr;
+        cudaError_t e = cudaMallocAsync(&tmp, bytes, st);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return host_fail(e == cudaErrorMemoryAllocation ? AH_ERR_OOM : AH_ERR_CUDA, cudaGetErrorString(e));
+        }
+        e = launch_gather_window<float>(lat_fields(L), L.cur, N, b, tmp, st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(w.out, tmp, bytes, cudaMemcpyDeviceToHost, st);
+        cudaFreeAsync(tmp, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) return host_fail(AH_ERR_CUDA, cudaGetErrorString(e));
+        return AH_OK;
+    }
+
+    // Per-shape one-time set-up of the kernels this engine launches.
+    cudaError_t prepare()
+    {
+        cudaError_t e = batch_shape_prepare(shape, num_sms, st, false);
+        if (e == cudaSuccess && two) e = batch_shape_prepare(shape2, num_sms, st, true);
+        return e;
     }
 
     // Observables of one lattice at its current step (the whole-lattice pass on
@@ -279,6 +418,12 @@ struct Engine {
         const View<float> v = lat_view(L);
         const Box b{ 0, 0, 0, L.N, L.N, L.N };
         const DiagCoef dc = host_diag_coef(L.cfg, L.step);
+        if (fused_diag_ctas(L.N) > nparts) {
+            char msg[160];
+            snprintf(msg, sizeof msg, "diagnostics scratch too small: the N=%d pass needs %d partials, %d allocated",
+                     L.N, fused_diag_ctas(L.N), nparts);
+            return host_fail(AH_ERR_CUDA, msg);
+        }
         cudaError_t e = launch_diag_whole<float>(v, L.N, dc, d_partials, nparts, d_result, list, diag_blocks, st);
         if (e == cudaSuccess) e = cudaMemcpyAsync(h_result, d_result, sizeof(DiagPartial), cudaMemcpyDeviceToHost, st);
         if (e == cudaSuccess)
@@ -303,11 +448,25 @@ int steps_to_event(const Lat &L)
     return next - L.step;
 }
 
-void advance_mirror(Lat &L, int R)
+// Host copy of the device-side step counter, buffers and Pi/E set of an
+// unfinished lattice after a round of R steps (R <= its steps to its next
+// stop); returns the steps it advanced.
+int advance_mirror(Lat &L, int R, bool two)
 {
-    const int d = std::min(R, L.nsteps - L.step);
-    L.step += d;
-    L.cur ^= (d & 1);
+    if (!two || !L.two) {
+        const int d = std::min(R, L.nsteps - L.step);
+        L.step += d;
+        L.cur ^= d & 1;
+        return d;
+    }
+    // R / 2 two-step passes (each swaps the phi/theta buffers and the Pi/E set),
+    // then, for an odd R, the single step if it leaves the lattice at its stop
+    const int P = R / 2;
+    const int single = (R % 2) && steps_to_event(L) - 2 * P == 1;
+    L.step += 2 * P + single;
+    L.cur ^= (P + single) & 1;
+    L.pe ^= P & 1;
+    return 2 * P + single;
 }
 
 ah_status check_batch_cfg(const ah_config &c)
@@ -321,16 +480,27 @@ ah_status check_batch_cfg(const ah_config &c)
 }  // namespace
 
 // ------------------------------------------------------------------ batch
-extern "C" ah_status ah_batch_run(const ah_config *cfgs, int32_t count, int32_t flags, ah_obs *series,
-                                  int64_t series_cap, int64_t *series_len, ah_batch_stats *stats)
+extern "C" ah_status ah_batch_run_ex(const ah_config *cfgs, int32_t count, int32_t flags, ah_obs *series,
+                                     int64_t series_cap, int64_t *series_len, ah_batch_stats *stats,
+                                     const ah_window *windows, int32_t nwindows)
 {
-    if (!cfgs || count < 1 || (series && (series_cap < 1 || !series_len)))
+    if (!cfgs || count < 1 || (series && (series_cap < 1 || !series_len)) || nwindows < 0 || (nwindows && !windows))
         return host_fail(AH_ERR_ARG, "ah_batch_run: bad arguments");
-    if (flags & ~(AH_BATCH_AUTOTUNE | AH_BATCH_NO_GRAPH)) return host_fail(AH_ERR_ARG, "ah_batch_run: unknown flags");
+    if (flags & ~(AH_BATCH_AUTOTUNE | AH_BATCH_NO_GRAPH | AH_BATCH_TWO_STEP))
+        return host_fail(AH_ERR_ARG, "ah_batch_run: unknown flags");
     for (int i = 0; i < count; ++i) {
         ah_status st = check_batch_cfg(cfgs[i]);
         if (st != AH_OK) return st;
     }
+    for (int k = 0; k < nwindows; ++k) {
+        if (windows[k].lattice < 0 || windows[k].lattice >= count)
+            return host_fail(AH_ERR_ARG, "window lattice index out of range");
+        ah_status st = check_window(windows[k], cfgs[windows[k].lattice].N);
+        if (st != AH_OK) return st;
+    }
+    const bool auto_pairs = (flags & AH_BATCH_TWO_STEP) != 0;
+    bool two = false;
+    for (int i = 0; i < count; ++i) two = two || lat_pairs(cfgs[i], auto_pairs);
     const double t0 = now_s();
     Engine eng;
     std::vector<Lat> lats(count);
@@ -341,17 +511,18 @@ extern "C" ah_status ah_batch_run(const ah_config *cfgs, int32_t count, int32_t 
             if (L.mem) cudaFreeAsync(L.mem, eng.st);
         eng.release();
     };
-    cudaError_t e = eng.init(!(flags & AH_BATCH_NO_GRAPH));
+    cudaError_t e = eng.init(!(flags & AH_BATCH_NO_GRAPH), two);
     for (int i = 0; i < count && e == cudaSuccess; ++i) {
         lats[i].cfg = cfgs[i];
         ptrs[i] = &lats[i];
-        e = lat_setup(lats[i], eng.st);
+        e = lat_setup(lats[i], lat_pairs(cfgs[i], auto_pairs), eng.st);
     }
     if (e != cudaSuccess) {
         cleanup();
         return host_fail(e == cudaErrorMemoryAllocation ? AH_ERR_OOM : AH_ERR_CUDA, cudaGetErrorString(e));
     }
-    // shape: the fastest over two timed steps of the whole batch (states restored after)
+    // shape: the fastest over two timed steps (two-step mode: two timed passes)
+    // of the whole batch, states restored after
     int best = 0;
     if (flags & AH_BATCH_AUTOTUNE) {
         float best_ms = 0.0f;
@@ -359,18 +530,21 @@ extern "C" ah_status ah_batch_run(const ah_config *cfgs, int32_t count, int32_t 
         cudaEvent_t a, b;
         cudaEventCreate(&a);
         cudaEventCreate(&b);
-        for (int s = 0; s < batch_shape_count() && e == cudaSuccess; ++s) {
+        const int nshapes = two ? batch2_shape_count() : batch_shape_count();
+        for (int s = 0; s < nshapes && e == cudaSuccess; ++s) {
             bool ok = true;
-            for (auto &L : lats) ok = ok && batch_shape_ok(s, L.N);
+            if (!two)
+                for (auto &L : lats) ok = ok && batch_shape_ok(s, L.N);
             if (!ok) continue;
-            eng.shape = s;
-            e = batch_shape_prepare(s, eng.num_sms, eng.st);
+            (two ? eng.shape2 : eng.shape) = s;
+            e = eng.prepare();
             if (e == cudaSuccess) e = eng.load(ptrs);
             if (e != cudaSuccess) break;
             eng.use_graph = false;
-            e = eng.steps(1);
+            const int R = two ? 4 : 2;
+            e = eng.steps(R / 2);
             if (e == cudaSuccess) e = cudaEventRecord(a, eng.st);
-            if (e == cudaSuccess) e = eng.steps(2);
+            if (e == cudaSuccess) e = eng.steps(R);
             if (e == cudaSuccess) e = cudaEventRecord(b, eng.st);
             if (e == cudaSuccess) e = cudaEventSynchronize(b);
             float ms = 0.0f;
@@ -385,8 +559,8 @@ extern "C" ah_status ah_batch_run(const ah_config *cfgs, int32_t count, int32_t 
         eng.launches = 0;
         eng.rounds = 0;
     }
-    eng.shape = best;
-    if (e == cudaSuccess) e = batch_shape_prepare(best, eng.num_sms, eng.st);
+    (two ? eng.shape2 : eng.shape) = best;
+    if (e == cudaSuccess) e = eng.prepare();
     if (e == cudaSuccess) e = eng.load(ptrs);
     if (e != cudaSuccess) {
         cleanup();
@@ -420,12 +594,13 @@ extern "C" ah_status ah_batch_run(const ah_config *cfgs, int32_t count, int32_t 
         for (int i = 0; i < count && st == AH_OK; ++i) {
             Lat &L = lats[i];
             if (L.step >= L.nsteps) continue;
-            advance_mirror(L, R);
+            advance_mirror(L, R, two);
             const bool due = L.step == L.nsteps || (L.cfg.diag_every > 0 && L.step % L.cfg.diag_every == 0);
             if (due) st = record(i);
         }
     }
     const double t2 = now_s();
+    for (int k = 0; k < nwindows && st == AH_OK; ++k) st = eng.gather(lats[windows[k].lattice], windows[k]);
     if (stats) {
         memset(stats, 0, sizeof *stats);
         stats->seconds = t2 - t1;
@@ -438,6 +613,12 @@ extern "C" ah_status ah_batch_run(const ah_config *cfgs, int32_t count, int32_t 
     }
     cleanup();
     return st;
+}
+
+extern "C" ah_status ah_batch_run(const ah_config *cfgs, int32_t count, int32_t flags, ah_obs *series,
+                                  int64_t series_cap, int64_t *series_len, ah_batch_stats *stats)
+{
+    return ah_batch_run_ex(cfgs, count, flags, series, series_cap, series_len, stats, nullptr, 0);
 }
 
 // ------------------------------------------------------------------ server
@@ -463,6 +644,7 @@ struct ah_server {
     // AH_FAKE_DEVICE_FAILURE_AFTER_ROUNDS at creation
     long long fail_after_rounds = 0, rounds_done = 0;
     bool broken = false;      // the worker stopped after a device error
+    bool auto_pairs = false;  // AH_BATCH_TWO_STEP: pair the lattices with N >= kPairMinN
 
     void run();
 };
@@ -529,7 +711,7 @@ void ah_server::run()
         }
         for (auto &L : admit) {
             const size_t bytes = L->bytes;
-            const cudaError_t e = lat_setup(*L, eng.st);
+            const cudaError_t e = lat_setup(*L, lat_pairs(L->cfg, auto_pairs), eng.st);
             std::lock_guard<std::mutex> lk(mu);
             if (e != cudaSuccess) {
                 used -= bytes;
@@ -559,26 +741,33 @@ void ah_server::run()
         if (e == cudaSuccess) e = cudaStreamSynchronize(eng.st);
         if (e != cudaSuccess) { fail_all(e); break; }
         ++rounds_done;
+        double su = 0.0;
+        for (auto *L : loaded) su += (double)L->nsites * advance_mirror(*L, R, eng.two);
         {
             std::lock_guard<std::mutex> lk(mu);
-            for (auto *L : loaded) stats.site_updates += (double)L->nsites * std::min(R, L->nsteps - L->step);
+            stats.site_updates += su;
             stats.launches = eng.launches;
         }
-        for (auto *L : loaded) advance_mirror(*L, R);
         // retire finished lattices with their final observables
         for (size_t i = 0; i < active.size();) {
             Lat &L = *active[i];
             if (L.step < L.nsteps) { ++i; continue; }
             ah_obs o;
             const ah_status ds = eng.diag(L, &o);
-            cudaFreeAsync(L.mem, eng.st);
             std::lock_guard<std::mutex> lk(mu);
             Result &r = results[L.id];
             if (r.state != RQ_CANCELLED) {          // a cancel that arrived during its last round wins
-                r.state = ds == AH_OK || ds == AH_ERR_NONFINITE ? RQ_DONE : RQ_FAILED;
+                // the caller's window buffers are written under the lock, so a
+                // cancel cannot return (and the caller free them) in between
+                bool ok = ds == AH_OK || ds == AH_ERR_NONFINITE;
+                for (const ah_window &w : L.wins)
+                    if (ok) ok = eng.gather(L, w) == AH_OK;
+                r.state = ok ? RQ_DONE : RQ_FAILED;
+                if (!ok) r.err = "final diagnostics or a window read-back failed";
                 r.obs = o;
                 r.t_done = now_s() - t_origin;
             }
+            cudaFreeAsync(L.mem, eng.st);
             used -= L.bytes;
             stats.completed += 1;
             active.erase(active.begin() + i);
@@ -591,7 +780,7 @@ extern "C" {
 
 ah_status ah_server_create(size_t hbm_budget_bytes, int32_t max_slots, int32_t flags, ah_server **out)
 {
-    if (!out || hbm_budget_bytes == 0 || max_slots < 1 || (flags & ~AH_BATCH_NO_GRAPH))
+    if (!out || hbm_budget_bytes == 0 || max_slots < 1 || (flags & ~(AH_BATCH_NO_GRAPH | AH_BATCH_TWO_STEP)))
         return host_fail(AH_ERR_ARG, "ah_server_create: bad arguments");
     *out = nullptr;
     ah_server *s = new (std::nothrow) ah_server();
@@ -601,8 +790,12 @@ ah_status ah_server_create(size_t hbm_budget_bytes, int32_t max_slots, int32_t f
     s->t_origin = now_s();
     if (const char *f = std::getenv("AH_FAKE_DEVICE_FAILURE_AFTER_ROUNDS")) s->fail_after_rounds = std::atoll(f);
     cudaGetDevice(&s->device);
-    cudaError_t e = s->eng.init(!(flags & AH_BATCH_NO_GRAPH));
-    if (e == cudaSuccess) e = batch_shape_prepare(0, s->eng.num_sms, s->eng.st);
+    s->auto_pairs = (flags & AH_BATCH_TWO_STEP) != 0;
+    // requests may ask for pairs themselves (AH_FLAG_TWO_STEP), so the engine
+    // can always run two-step passes; without paired lattices it launches the
+    // single-step kernel only, as in one-step mode
+    cudaError_t e = s->eng.init(!(flags & AH_BATCH_NO_GRAPH), true);
+    if (e == cudaSuccess) e = s->eng.prepare();
     if (e != cudaSuccess) {
         s->eng.release();
         delete s;
@@ -613,14 +806,19 @@ ah_status ah_server_create(size_t hbm_budget_bytes, int32_t max_slots, int32_t f
     return AH_OK;
 }
 
-ah_status ah_server_submit(ah_server *s, const ah_config *cfg, uint64_t *req_id)
+ah_status ah_server_submit_ex(ah_server *s, const ah_config *cfg, const ah_window *windows, int32_t nwindows,
+                              uint64_t *req_id)
 {
-    if (!s || !cfg || !req_id) return host_fail(AH_ERR_ARG, "ah_server_submit: null argument");
+    if (!s || !cfg || !req_id || nwindows < 0 || (nwindows && !windows))
+        return host_fail(AH_ERR_ARG, "ah_server_submit: null argument");
     ah_status st = check_batch_cfg(*cfg);
     if (st != AH_OK) return st;
+    for (int k = 0; k < nwindows; ++k)
+        if ((st = check_window(windows[k], cfg->N)) != AH_OK) return st;
     auto L = std::make_unique<Lat>();
     L->cfg = *cfg;
-    L->bytes = lattice_bytes(*cfg);
+    L->wins.assign(windows, windows + nwindows);
+    L->bytes = lattice_bytes(*cfg, lat_pairs(*cfg, s->auto_pairs));
     if (L->bytes > s->budget) return host_fail(AH_ERR_OOM, "request larger than the server's HBM budget");
     std::lock_guard<std::mutex> lk(s->mu);
     if (s->broken) return host_fail(AH_ERR_CUDA, "the server stopped after a device error");
@@ -635,6 +833,11 @@ ah_status ah_server_submit(ah_server *s, const ah_config *cfg, uint64_t *req_id)
     s->stats.submitted += 1;
     s->cv.notify_all();
     return AH_OK;
+}
+
+ah_status ah_server_submit(ah_server *s, const ah_config *cfg, uint64_t *req_id)
+{
+    return ah_server_submit_ex(s, cfg, nullptr, 0, req_id);
 }
 
 ah_status ah_server_poll(ah_server *s, uint64_t id, ah_obs *final_out, double *t_submit, double *t_done)

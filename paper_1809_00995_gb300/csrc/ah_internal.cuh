@@ -187,8 +187,8 @@ cudaError_t launch_diag_whole(const View<real> &v, int N, const DiagCoef &c, Dia
 
 // Host helpers of ah_api.cu shared with other translation units.
 KickCoef<float> host_kick_coef32(const ah_config &c, int64_t step);
-void host_carve32(Fields<float> &F, void *base, size_t nsites);
-size_t host_state_bytes32(size_t nsites);
+void host_carve32(Fields<float> &F, void *base, size_t nsites, bool spare = false);
+size_t host_state_bytes32(size_t nsites, bool spare = false);
 void host_fill_obs(const ah_config &c, int64_t step, int64_t n_sites, const DiagPartial &r, ah_obs *out);
 int64_t host_run_steps(const ah_config &c);    // round((tau_end - tau0) / dt)
 DiagCoef host_diag_coef(const ah_config &c, int64_t step);
@@ -196,20 +196,64 @@ ah_status host_validate(const ah_config &c);
 ah_status host_fail(ah_status st, const char *msg);
 
 // Batched fused step (FP32): one descriptor per lattice, work items (lattice,
-// tile index), device-side step counters.
+// tile index), device-side step counters.  q[0] = { F.pir, F.pii, F.el[0..2] };
+// q[1] = F.spare, the second Pi/E set of the two-step pass (null unless the
+// batch runs two steps per launch).
 struct BatchLattice {
     Fields<float> F;
-    int N, zc, tiles_x, tiles_y, nchunk;
+    float *q[2][5];
+    int N, zc, tiles_x, tiles_y, nchunk;       // single-step work items
+    int zc2, tiles2_x, tiles2_y, nchunk2;      // two-step work items
     int nsteps;                      // steps this lattice runs in total
+    int diag_every;                  // diagnostic cadence (0: at the end only)
+    int pairs;                       // advanced two steps per launch (two-step batches)
     const KickCoef<float> *coefs;    // [nsteps] coefficients of each step
 };
-struct BatchState { int step; int cur; };
+// step: steps done; cur: phi/theta buffer holding phi^n, theta^n; pe: Pi/E set
+// (index into BatchLattice::q) holding Pi^{n-1/2}, E^{n-1/2}
+struct BatchState { int step; int cur; int pe; };
+// Next stop of a lattice at step n: its next diagnostic point or its end.  In
+// two-step batches a lattice advances in pairs of steps and takes a single
+// step only when one step is left to its next stop, so the grouping of its
+// steps does not depend on the other lattices of the batch.
+__host__ __device__ inline int batch_stop(const BatchLattice &B, int n)
+{
+    if (B.diag_every <= 0) return B.nsteps;
+    const long long d = ((long long)n / B.diag_every + 1) * B.diag_every;
+    return d < B.nsteps ? (int)d : B.nsteps;
+}
+// Which lattices a batched launch advances, at step n.  A two-step pass: the
+// lattices stepped in pairs with two or more steps to their next stop.  A
+// single-step launch: BATCH_ALL every unfinished lattice (one step per launch
+// throughout); BATCH_UNPAIRED the unfinished lattices not stepped in pairs;
+// BATCH_ROUND_END those and the paired lattices one step before their stop.
+enum { BATCH_ALL = 0, BATCH_UNPAIRED = 1, BATCH_ROUND_END = 2 };
+__host__ __device__ inline bool batch_takes_pair(const BatchLattice &B, int n)
+{
+    return B.pairs && n + 2 <= batch_stop(B, n);
+}
+__host__ __device__ inline bool batch_takes_single(const BatchLattice &B, int n, int mode)
+{
+    if (mode == BATCH_ALL || !B.pairs) return n < B.nsteps;
+    return mode == BATCH_ROUND_END && n + 1 == batch_stop(B, n);
+}
 int batch_shape_count();
 bool batch_shape_ok(int shape, int N);
 void batch_tiles(int shape, int N, int *tx, int *ty);
-cudaError_t batch_shape_prepare(int shape, int num_sms, cudaStream_t st);
+// Per-shape one-time set-up (kernel attributes, occupancy) of the batched
+// single-step kernel, or of the batched two-step pass if `two`, outside any
+// stream capture.
+cudaError_t batch_shape_prepare(int shape, int num_sms, cudaStream_t st, bool two = false);
+// mode: which lattices take part (BATCH_ALL, BATCH_UNPAIRED, BATCH_ROUND_END).
 cudaError_t launch_fused_batch(int shape, const BatchLattice *lat, BatchState *state, int nlat, const int2 *items,
-                               const int *nitems, unsigned int *counter, int num_sms, cudaStream_t st);
+                               const int *nitems, unsigned int *counter, int num_sms, cudaStream_t st,
+                               int mode = BATCH_ALL);
+// Batched two-step pass (two leapfrog steps of every lattice per launch),
+// shapes 0 (32 x 8 CTA tile, 3 CTAs per SM) and 1 (32 x 12, 2 per SM).
+int batch2_shape_count();
+void batch2_tiles(int shape, int N, int *tx, int *ty);
+cudaError_t launch_fused2_batch(int shape, const BatchLattice *lat, BatchState *state, int nlat, const int2 *items,
+                                const int *nitems, unsigned int *counter, int num_sms, cudaStream_t st);
 
 // Fused step with paired FP32 arithmetic (N even), shapes 0..4.
 bool pair_shape_ok(int N);
@@ -226,8 +270,11 @@ bool tma_shape_ok(int N);
 size_t tma_smem_bytes();
 cudaError_t make_tma_map(CUtensorMap *m, const float *base, int N);
 // minb: resident CTAs per SM the registers must allow (2 or 3); *err is set to 1
-// if a bounded wait gave up.
+// if a bounded wait (wait_limit clock cycles per wait) gave up.  drop_q >= 0
+// (fault injection for tests) leaves the copy of that Pi/E plane of every CTA
+// unissued, so its wait gives up.
+constexpr long long kTmaWaitLimit = 1LL << 32;    // about 2 s at 2 GHz
 cudaError_t launch_fused_tma(const TmaMaps &maps, const View<float> &v, int N, const KickCoef<float> &c,
-                             int *err, int minb, int min_chunk, cudaStream_t st);
+                             int *err, int minb, int min_chunk, long long wait_limit, int drop_q, cudaStream_t st);
 
 }  // namespace ah

@@ -502,7 +502,7 @@ __global__ void __launch_bounds__(256) k_fused_diag(View<real> v, int N, int zc,
 template <int TY, int RX, int MINB>
 __global__ void __launch_bounds__(256, MINB)
 k_fused_batch(const BatchLattice *lat, BatchState *state, const int2 *items, const int *nitems,
-              unsigned int *counter)
+              unsigned int *counter, int mode)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ int s_item;
@@ -516,13 +516,14 @@ k_fused_batch(const BatchLattice *lat, BatchState *state, const int2 *items, con
         const int L = items[it].x, local = items[it].y;
         const BatchLattice &B = lat[L];
         const int step = state[L].step;
-        if (step >= B.nsteps) continue;
+        if (!batch_takes_single(B, step, mode)) continue;
         const int cur = state[L].cur, o = 1 - cur;
+        float *const *q = B.q[state[L].pe];
         View<float> v;
         v.phr = B.F.phr[cur]; v.phi = B.F.phi[cur];
         v.th1 = B.F.th[cur][0]; v.th2 = B.F.th[cur][1]; v.th3 = B.F.th[cur][2];
-        v.pir = B.F.pir; v.pii = B.F.pii;
-        v.e1 = B.F.el[0]; v.e2 = B.F.el[1]; v.e3 = B.F.el[2];
+        v.pir = q[0]; v.pii = q[1];
+        v.e1 = q[2]; v.e2 = q[3]; v.e3 = q[4];
         v.ophr = B.F.phr[o]; v.ophi = B.F.phi[o];
         v.oth1 = B.F.th[o][0]; v.oth2 = B.F.th[o][1]; v.oth3 = B.F.th[o][2];
         const int bx = local % B.tiles_x, by = (local / B.tiles_x) % B.tiles_y, bz = local / (B.tiles_x * B.tiles_y);
@@ -531,12 +532,14 @@ k_fused_batch(const BatchLattice *lat, BatchState *state, const int2 *items, con
     }
 }
 
-// After a batched step: every unfinished lattice moves to its next step and
-// swaps its phi/theta buffers; the work counter is reset.
-__global__ void k_batch_advance(const BatchLattice *lat, BatchState *state, int nlat, unsigned int *counter)
+// After a batched step: every lattice that took part (batch_takes_single)
+// moves to its next step and swaps its phi/theta buffers; the work counter is
+// reset.
+__global__ void k_batch_advance(const BatchLattice *lat, BatchState *state, int nlat, unsigned int *counter,
+                                int mode)
 {
     for (int L = threadIdx.x; L < nlat; L += blockDim.x) {
-        if (state[L].step < lat[L].nsteps) {
+        if (batch_takes_single(lat[L], state[L].step, mode)) {
             state[L].step += 1;
             state[L].cur ^= 1;
         }
@@ -745,7 +748,7 @@ constexpr BatchShape kBatchShapes[] = { { 8, 1, 4 }, { 16, 1, 2 }, { 8, 2, 2 } }
 
 template <int TY, int RX, int MINB>
 cudaError_t launch_batch_shape(const BatchLattice *lat, BatchState *state, int nlat, const int2 *items,
-                               const int *nitems, unsigned int *counter, int num_sms, cudaStream_t st)
+                               const int *nitems, unsigned int *counter, int num_sms, cudaStream_t st, int mode)
 {
     using G = Geo<float, TY, RX>;
     static int blocks_per_sm_dev[64] = {};      // per device
@@ -759,8 +762,9 @@ cudaError_t launch_batch_shape(const BatchLattice *lat, BatchState *state, int n
         if (e != cudaSuccess) return e;
         blocks_per_sm = b < 1 ? 1 : b;
     }
-    k_fused_batch<TY, RX, MINB><<<num_sms * blocks_per_sm, 256, G::smem, st>>>(lat, state, items, nitems, counter);
-    k_batch_advance<<<1, 256, 0, st>>>(lat, state, nlat, counter);
+    k_fused_batch<TY, RX, MINB><<<num_sms * blocks_per_sm, 256, G::smem, st>>>(lat, state, items, nitems, counter,
+                                                                              mode);
+    k_batch_advance<<<1, 256, 0, st>>>(lat, state, nlat, counter, mode);
     return cudaGetLastError();
 }
 }  // namespace
@@ -769,7 +773,7 @@ int batch_shape_count() { return (int)(sizeof(kBatchShapes) / sizeof(kBatchShape
 
 // Per-shape one-time set-up (shared-memory attribute, occupancy) done outside
 // any stream capture: a launch of an empty work list.
-cudaError_t batch_shape_prepare(int shape, int num_sms, cudaStream_t st)
+cudaError_t batch_shape_prepare(int shape, int num_sms, cudaStream_t st, bool two)
 {
     // a few bytes of device scratch per device, kept for the life of the process
     static BatchState *d_dummy_dev[64] = {};
@@ -795,6 +799,7 @@ cudaError_t batch_shape_prepare(int shape, int num_sms, cudaStream_t st)
         d_dummy = a; d_zero = z; d_cnt = c;
     }
     // nlat = 0: the advance kernel touches no lattice; nitems = 0: no work
+    if (two) return launch_fused2_batch(shape, nullptr, d_dummy, 0, nullptr, d_zero, d_cnt, num_sms, st);
     return launch_fused_batch(shape, nullptr, d_dummy, 0, nullptr, d_zero, d_cnt, num_sms, st);
 }
 
@@ -808,12 +813,13 @@ void batch_tiles(int shape, int N, int *tx, int *ty)
 bool batch_shape_ok(int shape, int N) { return kBatchShapes[shape].rx == 1 || N % 2 == 0; }
 
 cudaError_t launch_fused_batch(int shape, const BatchLattice *lat, BatchState *state, int nlat, const int2 *items,
-                               const int *nitems, unsigned int *counter, int num_sms, cudaStream_t st)
+                               const int *nitems, unsigned int *counter, int num_sms, cudaStream_t st,
+                               int mode)
 {
     switch (shape) {
-    case 0: return launch_batch_shape<8, 1, 4>(lat, state, nlat, items, nitems, counter, num_sms, st);
-    case 1: return launch_batch_shape<16, 1, 2>(lat, state, nlat, items, nitems, counter, num_sms, st);
-    case 2: return launch_batch_shape<8, 2, 2>(lat, state, nlat, items, nitems, counter, num_sms, st);
+    case 0: return launch_batch_shape<8, 1, 4>(lat, state, nlat, items, nitems, counter, num_sms, st, mode);
+    case 1: return launch_batch_shape<16, 1, 2>(lat, state, nlat, items, nitems, counter, num_sms, st, mode);
+    case 2: return launch_batch_shape<8, 2, 2>(lat, state, nlat, items, nitems, counter, num_sms, st, mode);
     default: return cudaErrorInvalidValue;
     }
 }

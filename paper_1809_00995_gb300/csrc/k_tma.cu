@@ -20,8 +20,10 @@
 //    update of plane z together with the links of plane z+2.
 //
 // Requires N % 32 == 0 (whole tiles; TMA boxes never cross the lattice edge).
-// Every mbarrier wait is bounded (about 2 s); on timeout the CTA records an
-// error in *err, stops issuing work and returns after a bounded drain.
+// Every mbarrier wait is bounded (wait_limit clock cycles, 2^32 = about 2 s by
+// default); on timeout the CTA records an error in *err, stops issuing copies,
+// waits (each wait again bounded, 2^24 cycles) for the last copy it issued
+// into each ring stage and returns.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
@@ -94,7 +96,8 @@ struct Smem {
 
 template <int MINB>
 __global__ void __launch_bounds__(NT, MINB)
-k_fused_tma(const __grid_constant__ TmaMaps maps, View<float> v, int N, int zc, KickCoef<float> c, int *err)
+k_fused_tma(const __grid_constant__ TmaMaps maps, View<float> v, int N, int zc, KickCoef<float> c, int *err,
+            long long wait_limit, int drop_q)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     Smem &S = *reinterpret_cast<Smem *>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
@@ -144,18 +147,27 @@ k_fused_tma(const __grid_constant__ TmaMaps maps, View<float> v, int N, int zc, 
     }
     __syncthreads();
 
-    // producer (thread 0): plane index f of the link planes is z0 - 1 + f
+    // producer (thread 0): plane index f of the link planes is z0 - 1 + f.
+    // f_last / q_last: the last plane whose copy went to each ring stage (-1:
+    // none), so that an early exit waits exactly for the copies in flight.
+    int f_last[FS], q_last[QS];
+    for (int s = 0; s < FS; ++s) f_last[s] = -1;
+    for (int s = 0; s < QS; ++s) q_last[s] = -1;
     auto issue_F = [&](int f) {
         if (f >= nF) return;
         const int s = f % FS, z = wrapm(z0 - 1 + f, N);
         mbar_arrive_tx(&S.fbar[s], 5 * BOX * 4);
         for (int k = 0; k < 5; ++k) tma3d(S.F[s][k], &maps.f[k], &S.fbar[s], x0, y0, z);
+        f_last[s] = f;
     };
+    // drop_q (fault injection for tests, -1 otherwise): the copy of Pi/E plane
+    // drop_q is never issued, so the wait for it can only give up
     auto issue_Q = [&](int q) {
-        if (q >= nz) return;
+        if (q >= nz || q == drop_q) return;
         const int s = q % QS, z = z0 + q;
         mbar_arrive_tx(&S.qbar[s], 5 * BOX * 4);
         for (int k = 0; k < 5; ++k) tma3d(S.Q[s][k], &maps.q[k], &S.qbar[s], x0, y0, z);
+        q_last[s] = q;
     };
     if (tid == 0) {
         for (int f = 0; f < FS; ++f) issue_F(f);
@@ -175,7 +187,7 @@ k_fused_tma(const __grid_constant__ TmaMaps maps, View<float> v, int N, int zc, 
     // A(f): links and phi of link plane f into ring slot f % 3; returns own theta
     auto phase_A = [&](int f, float th_own[3], cpx &ph_own) {
         const int s = f % FS, u = f % 3;
-        if (!mbar_wait(&S.fbar[s], (f / FS) & 1)) atomicExch(&S.err, 1);
+        if (!mbar_wait(&S.fbar[s], (f / FS) & 1, wait_limit)) atomicExch(&S.err, 1);
         const int i = wy * TX + lx;
         ph_own = { S.F[s][0][i], S.F[s][1][i] };
 #pragma unroll
@@ -249,7 +261,7 @@ k_fused_tma(const __grid_constant__ TmaMaps maps, View<float> v, int N, int zc, 
         // C: kicks and drifts of the own site of plane z
         {
             const int qs = k % QS;
-            const bool landed = mbar_wait(&S.qbar[qs], (k / QS) & 1);
+            const bool landed = mbar_wait(&S.qbar[qs], (k / QS) & 1, wait_limit);
             if (!landed) atomicExch(&S.err, 1);
             const int i = wy * TX + lx;
             const float pr = S.Q[qs][0][i], pim = S.Q[qs][1][i];
@@ -311,9 +323,13 @@ k_fused_tma(const __grid_constant__ TmaMaps maps, View<float> v, int N, int zc, 
     if (!ok) {
         if (tid == 0) {
             atomicExch(err, 1);
-            // bounded drain of copies still in flight into this CTA's shared memory
-            for (int s = 0; s < FS; ++s) mbar_wait(&S.fbar[s], 0, 1LL << 24), mbar_wait(&S.fbar[s], 1, 1LL << 24);
-            for (int s = 0; s < QS; ++s) mbar_wait(&S.qbar[s], 0, 1LL << 24), mbar_wait(&S.qbar[s], 1, 1LL << 24);
+            // drain: wait (bounded) for the last copy issued into each stage, so
+            // that no copy into this CTA's shared memory is in flight at exit (the
+            // wait returns at once for a copy that has landed)
+            for (int s = 0; s < FS; ++s)
+                if (f_last[s] >= 0) mbar_wait(&S.fbar[s], (f_last[s] / FS) & 1, 1LL << 24);
+            for (int s = 0; s < QS; ++s)
+                if (q_last[s] >= 0) mbar_wait(&S.qbar[s], (q_last[s] / QS) & 1, 1LL << 24);
         }
         __syncthreads();
     }
@@ -321,7 +337,7 @@ k_fused_tma(const __grid_constant__ TmaMaps maps, View<float> v, int N, int zc, 
 
 template <int MINB>
 cudaError_t launch_minb(const TmaMaps &maps, const View<float> &v, int N, const KickCoef<float> &c, int *err,
-                        int min_chunk, cudaStream_t st)
+                        int min_chunk, long long wait_limit, int drop_q, cudaStream_t st)
 {
     static unsigned long long configured = 0;   // per device
     const unsigned long long dev_bit = 1ULL << device_slot();
@@ -336,7 +352,8 @@ cudaError_t launch_minb(const TmaMaps &maps, const View<float> &v, int N, const 
     nch = max(1, min(nch, N / min_chunk));
     const int zc = (N + nch - 1) / nch;
     nch = (N + zc - 1) / zc;
-    k_fused_tma<MINB><<<dim3(tx, ty, nch), NT, sizeof(Smem) + 128, st>>>(maps, v, N, zc, c, err);
+    k_fused_tma<MINB><<<dim3(tx, ty, nch), NT, sizeof(Smem) + 128, st>>>(maps, v, N, zc, c, err, wait_limit,
+                                                                         drop_q);
     return cudaGetLastError();
 }
 
@@ -347,11 +364,11 @@ bool tma_shape_ok(int N) { return N % TX == 0 && N % TY == 0 && N >= TX; }
 size_t tma_smem_bytes() { return sizeof(Smem) + 128; }
 
 cudaError_t launch_fused_tma(const TmaMaps &maps, const View<float> &v, int N, const KickCoef<float> &c, int *err,
-                             int minb, int min_chunk, cudaStream_t st)
+                             int minb, int min_chunk, long long wait_limit, int drop_q, cudaStream_t st)
 {
-    if (!tma_shape_ok(N)) return cudaErrorInvalidValue;
-    if (minb == 3) return launch_minb<3>(maps, v, N, c, err, min_chunk, st);
-    return launch_minb<2>(maps, v, N, c, err, min_chunk, st);
+    if (!tma_shape_ok(N) || wait_limit < 0) return cudaErrorInvalidValue;
+    if (minb == 3) return launch_minb<3>(maps, v, N, c, err, min_chunk, wait_limit, drop_q, st);
+    return launch_minb<2>(maps, v, N, c, err, min_chunk, wait_limit, drop_q, st);
 }
 
 // Tensor maps of one FP32 field array (N^3, x fastest) with box 32 x 8 x 1.

@@ -120,6 +120,125 @@ def test_batch_diagnostics_of_sides_with_large_diag_grids(N):
     close_obs(series[0][-1], ref[-1])
 
 
+# ------------------------------------------------------------- fields vs the oracle
+TOL32 = 1e-5     # per component max|f_gpu - f_ref| / max(max|f_ref|, 1), FP32 state, 20 steps
+
+
+def rel_err(got, ref):
+    return [float(np.max(np.abs(got[c] - ref[c])) / max(np.max(np.abs(ref[c])), 1.0)) for c in range(10)]
+
+
+def short_config(N, era, s, seed, nsteps, **kw):
+    """A run of `nsteps` steps from tau0 = 1 with the scale-factor normalisation of
+    the full run (tau_ref = N dx / 2)."""
+    c = ah.config(N, era=era, s=s, seed=seed, **kw)
+    c.tau_ref = N * c.dx / 2.0
+    c.tau_end = c.tau0 + nsteps * c.dt
+    return c
+
+
+def oracle_fields(cfg, nsteps, M=None, origin=(0, 0, 0)):
+    """The oracle's evolution of the FP32 state's initial values (a window of M^3
+    sites at `origin`, default the whole lattice) over nsteps steps."""
+    p = O.Params(N=cfg.N, era=cfg.era, s=cfg.s, seed=cfg.seed, tau_ref=cfg.tau_ref,
+                 wrap_theta=bool(cfg.flags & ah.AH_FLAG_WRAP_THETA),
+                 core_growth=bool(cfg.flags & ah.AH_FLAG_CORE_GROWTH))
+    f = O.init(p, M=M, origin=origin).astype(np.float32).astype(np.float64)
+    return O.evolve(p, f, 0, nsteps), p
+
+
+@pytest.mark.parametrize("paired,flags", [("none", 0), ("all", 0), ("some", ah.AH_BATCH_AUTOTUNE)])
+def test_batch_fields_match_oracle(paired, flags):
+    """Every lattice of a mixed batch (ragged sides that leave partial tiles and z
+    chunks, both eras, s = 0 and 1, 20 or 21 steps so that a lattice stepped in
+    pairs also ends with one single step) equals the oracle field by field after
+    its run: per component within 1e-5 of max(max|f|, 1) (FP32 state, Eqs.
+    up_pi, up_E, up_phi, up_A), and its final observables equal the oracle's on
+    the returned snapshot (sums to the FP32 tolerance, windings exactly).  The
+    lattices are stepped one step per launch, all in pairs (two-step passes,
+    AH_FLAG_TWO_STEP), or half of them in pairs."""
+    Ns = [12, 17, 20, 33, 24, 9]
+    cfgs = []
+    for i, N in enumerate(Ns):
+        era, s = ERAS[i % len(ERAS)]
+        pair = paired == "all" or (paired == "some" and i % 3 != 1)
+        cfgs.append(short_config(N, era, s, 300 + i, 20 + (i % 2), diag_every=0,
+                                 flags=ah.AH_FLAG_TWO_STEP if pair else 0))
+    wins = [(i, 0, 0, 0, c.N, c.N, c.N) for i, c in enumerate(cfgs)]
+    series, st, fields = ah.ah_batch_run_ex(cfgs, wins, flags=flags)
+    assert st["launches"] > 0
+    for i, c in enumerate(cfgs):
+        n = 20 + (i % 2)
+        ref, p = oracle_fields(c, n)
+        err = rel_err(fields[i], ref)
+        assert max(err) <= TOL32, (c.N, err)
+        go = series[i][-1]
+        assert go["step"] == n
+        oo = O.observables(p, fields[i], n)
+        S1 = abs(oo["sum_rho"])
+        for k, name in enumerate(["sum_L", "sum_rho", "sum_p", "sum_K", "sum_G2", "sum_V", "sum_Eel", "sum_B"]):
+            assert abs(go["sums"][k] - oo[name]) <= 1e-5 * abs(oo[name]) + 2e-6 * S1, (c.N, name)
+        assert list(go["wind_abs_plane"]) == list(oo["sum_abs_W_plane"])
+        assert go["n_pierced"] == oo["n_pierced"]
+
+
+def test_batch_two_step_equals_one_step_per_launch():
+    """Two steps per batched launch and one step per launch evaluate the same
+    formulas: the same lattices agree to FP32 rounding (contractions may differ),
+    including a run with compact link phases and one with core growth."""
+    cfgs = [short_config(20, ah.AH_MATTER, 1.0, 41, 30, diag_every=0),
+            short_config(27, ah.AH_RADIATION, 0.0, 42, 31, diag_every=0, flags=ah.AH_FLAG_WRAP_THETA),
+            short_config(16, ah.AH_RADIATION, 0.0, 43, 25, diag_every=0, flags=ah.AH_FLAG_CORE_GROWTH)]
+    cfgs[2].tau_ref = cfgs[2].tau0 + 1.25       # the switch from s to 1 falls inside the run
+    wins = [(i, 0, 0, 0, c.N, c.N, c.N) for i, c in enumerate(cfgs)]
+    _, _, one = ah.ah_batch_run_ex(cfgs, wins, flags=0)
+    for c in cfgs:
+        c.flags |= ah.AH_FLAG_TWO_STEP
+    _, st, two = ah.ah_batch_run_ex(cfgs, wins, flags=0)
+    for a, b in zip(one, two):
+        assert max(rel_err(b, a)) <= 1e-5
+    # rounds of 25, 6 and 1 steps (each lattice keeps its steps in pairs and
+    # takes a single step only one step before its end): 12 + 3 two-step passes
+    # and 2 single-step launches, two kernels (step and advance) per launch
+    assert st["launches"] == 2 * (12 + 1 + 3 + 1)
+
+
+def test_batch_1024cubed_light_cone_windows():
+    """A 1024^3 FP32 lattice (matter era, s = 1, seed 3: the configuration of the
+    throughput target) run through the batched engine with AH_BATCH_TWO_STEP
+    (lattices of side >= 512 in pairs, the others one step per launch) and
+    autotuned shapes, beside two small lattices: after 20 steps three 16^3
+    windows (two across the periodic seam) equal the oracle's evolution of the
+    (16 + 2 * 20)^3 windows of the same initial lattice; the small lattices equal
+    the oracle whole."""
+    N, k, b = 1024, 20, 16
+    big = short_config(N, ah.AH_MATTER, 1.0, 3, k, diag_every=0)
+    small = [short_config(24, ah.AH_RADIATION, 0.0, 5, k, diag_every=0),
+             short_config(13, ah.AH_MATTER, 0.0, 6, k + 1, diag_every=0)]
+    cfgs = [big] + small
+    orgs = [(1016, 5, 1019), (300, 1010, 7), (511, 512, 640)]
+    wins = [(0, *o, b, b, b) for o in orgs] + [(1, 0, 0, 0, 24, 24, 24), (2, 0, 0, 0, 13, 13, 13)]
+    series, _, fields = ah.ah_batch_run_ex(cfgs, wins, flags=ah.AH_BATCH_TWO_STEP | ah.AH_BATCH_AUTOTUNE,
+                                           series_cap=2)
+    for w, org in enumerate(orgs):
+        M = b + 2 * k
+        ref, _ = oracle_fields(big, k, M=M, origin=[(o - k) % N for o in org])
+        assert max(rel_err(fields[w], ref[:, k:k + b, k:k + b, k:k + b])) <= TOL32, org
+    for j, c in enumerate(small):
+        ref, _ = oracle_fields(c, k + j)
+        assert max(rel_err(fields[3 + j], ref)) <= TOL32, c.N
+    o = series[0][-1]
+    assert o["step"] == k and o["n_sites"] == N ** 3 and o["nonfinite"] == 0 and o["gauss_rel"] < 1e-5
+
+
+def test_batch_window_arguments_are_checked():
+    c = short_config(8, ah.AH_RADIATION, 0.0, 1, 2)
+    for w in [(1, 0, 0, 0, 4, 4, 4), (0, 0, 0, 0, 9, 4, 4), (0, 0, 0, 0, 0, 4, 4)]:
+        with pytest.raises(ah.AhError) as e:
+            ah.ah_batch_run_ex([c], [w])
+        assert e.value.status == ah.AH_ERR_ARG
+
+
 def test_batch_rejects_bad_configs():
     with pytest.raises(ah.AhError) as e:
         ah.ah_batch_run([ah.config(16, precision=ah.AH_FP64)])
@@ -139,21 +258,40 @@ def wait_done(srv, rid, timeout=120.0):
     raise TimeoutError(rid)
 
 
-def test_server_results_same_alone_and_in_the_mix():
+@pytest.mark.parametrize("pairs", [False, True])
+def test_server_results_same_alone_and_in_the_mix(pairs):
     """Requests arriving while others run are admitted as slots free up, stepped
-    together, and each final result equals the same request served alone."""
+    together, and each final result equals the same request served alone (also
+    when some requests are stepped in pairs, AH_FLAG_TWO_STEP: each keeps its
+    own grouping of steps whatever the mix).  One request, admitted while others
+    run, returns its final fields, which equal the oracle's run of the same
+    configuration."""
     cfgs = mixed_configs([32, 16, 24, 40, 12, 20, 28, 36], diag_every=0, seed0=500)
-    with ah.Server(hbm_budget_bytes=8 << 30, max_slots=3) as srv:
+    probe = short_config(22, ah.AH_MATTER, 1.0, 77, 21, diag_every=0)
+    if pairs:
+        for c in cfgs[::2] + [probe]:
+            c.flags |= ah.AH_FLAG_TWO_STEP
+    flags = 0
+    with ah.Server(hbm_budget_bytes=8 << 30, max_slots=3, flags=flags) as srv:
         ids = []
         for i, c in enumerate(cfgs):
             ids.append(srv.submit(c))
             if i % 3 == 2:
                 time.sleep(0.02)          # later requests arrive while earlier ones run
+            if i == 4:
+                pid, (pf,) = srv.submit_ex(probe, [(0, 0, 0, 22, 22, 22)])
         results = [wait_done(srv, rid) for rid in ids]
+        pobs, _, _ = wait_done(srv, pid)
+        ref, p = oracle_fields(probe, 21)
+        assert max(rel_err(pf, ref)) <= TOL32
+        assert pobs["step"] == 21
+        oo = O.observables(p, pf, 21)
+        assert list(pobs["wind_abs_plane"]) == list(oo["sum_abs_W_plane"])
+        assert abs(pobs["sums"][1] - oo["sum_rho"]) <= 1e-5 * abs(oo["sum_rho"])
         st = srv.stats()
-        assert st["completed"] == len(cfgs) and st["running"] == 0 and st["queued"] == 0
+        assert st["completed"] == len(cfgs) + 1 and st["running"] == 0 and st["queued"] == 0
         assert st["hbm_used"] == 0 and st["site_updates"] > 0
-    with ah.Server(hbm_budget_bytes=8 << 30, max_slots=1) as srv:
+    with ah.Server(hbm_budget_bytes=8 << 30, max_slots=1, flags=flags) as srv:
         for c, (obs, ts, td) in zip(cfgs, results):
             assert td >= ts
             alone, _, _ = wait_done(srv, srv.submit(c))

@@ -73,8 +73,9 @@ __device__ __forceinline__ void fused_tile(const View<real> &v, int N, int zc, c
     const int z0 = bz * zc;
     constexpr bool STEP = MODE == MODE_STEP, DIAG = MODE == MODE_DIAG;
     // per-thread diagnostic accumulators (MODE_DIAG): the energy sums of
-    // ah_obs (compensated, state precision), the Gauss residual sums and max
-    // (FP64), max |theta|, winding counters, non-finite sites
+    // ah_obs 3..13 (compensated, state precision; 0..2 follow from 3..7), the
+    // Gauss residual sums and max (FP64), max |theta|, winding counters,
+    // non-finite sites
     Acc<real> dacc[14];
     real dtmax = real(0);
     int dic[kNumInt] = { 0, 0, 0, 0, 0, 0, 0, 0 };   // per thread at most 3 x 2048 planes x |W| <= 2
@@ -98,7 +99,11 @@ __device__ __forceinline__ void fused_tile(const View<real> &v, int N, int zc, c
         if constexpr (DIAG) {
             double accd[kNumSums];
 #pragma unroll
-            for (int k = 0; k < 14; ++k) accd[k] = dacc[k].value();
+            for (int k = 3; k < 14; ++k) accd[k] = dacc[k].value();
+            // the sums of L, rho and p are linear in those of K, G2, V, E_el, B
+            accd[0] = accd[3] - accd[4] - accd[5] + accd[6] - accd[7];
+            accd[1] = accd[3] + accd[4] + accd[5] + accd[6] + accd[7];
+            accd[2] = accd[3] - accd[4] * (1.0 / 3.0) - accd[5] + (accd[6] + accd[7]) * (1.0 / 3.0);
             if constexpr (sizeof(real) == 4) {
                 dg2 = fg2.value() * 0x1p-60;
                 dgs2 = fgs2.value() * 0x1p-60;
@@ -359,6 +364,17 @@ __device__ __forceinline__ void fused_tile(const View<real> &v, int N, int zc, c
                 ez1[m] = edge(F1[e], U1p[e], F1[e + 1]);
                 ez2[m] = edge(F1[e], U1p[NE + e], F1[e + EX]);
             }
+            // MODE_DIAG: a plaquette whose four edges all have |Arg| < pi/4
+            // has W = 0; where that holds for the three plaquettes of every
+            // site of the warp, as in smooth regions, the carry chains are
+            // skipped (the vote is taken with the whole warp converged)
+            [[maybe_unused]] bool smooth_warp = false;
+            if constexpr (DIAG) {
+                const Z a21 = sE[NE + e + 1], a31 = sE[2 * NE + e + 1], a12 = sE[e + EX], a32 = sE[2 * NE + e + EX];
+                smooth_warp = __all_sync(0xffffffffu, small_args(ed1[m], a21, a12, ed2[m]) &
+                                                          small_args(ed1[m], a31, ez1[m], ed3[m]) &
+                                                          small_args(ed2[m], a32, ez2[m], ed3[m]));
+            }
             if constexpr (DIAG) if (wr[m / RX]) {
                 const real K = pr[m] * pr[m] + pim[m] * pim[m];
                 const real d1r = w1.r - f0.r, d1i = w1.i - f0.i, d2r = w2.r - f0.r, d2i = w2.i - f0.i;
@@ -372,7 +388,7 @@ __device__ __forceinline__ void fused_tile(const View<real> &v, int N, int zc, c
                 const real L = K - G2 - V + Eel - B;
                 const real rho = K + G2 + V + Eel + B;
                 const real pp = K - G2 * real(1.0 / 3.0) - V + (Eel + B) * real(1.0 / 3.0);
-                dacc[0].add(L); dacc[1].add(rho); dacc[2].add(pp); dacc[3].add(K); dacc[4].add(G2);
+                dacc[3].add(K); dacc[4].add(G2);
                 dacc[5].add(V); dacc[6].add(Eel); dacc[7].add(B); dacc[8].add(K * V); dacc[9].add(G2 * V);
                 dacc[10].add(K * L); dacc[11].add(G2 * L); dacc[12].add(pp * L); dacc[13].add(rho * L);
                 dtmax = fmax(dtmax, fmax(fabs(th_0[m][0]), fmax(fabs(th_0[m][1]), fabs(th_0[m][2]))));
@@ -415,9 +431,12 @@ __device__ __forceinline__ void fused_tile(const View<real> &v, int N, int zc, c
                 // neighbours' from shared memory
                 const Z z2_1 = sE[NE + e + 1], z3_1 = sE[2 * NE + e + 1];
                 const Z z1_2 = sE[e + EX], z3_2 = sE[2 * NE + e + EX];
-                const int wq[3] = { winding_scaled(ed1[m], z2_1, z1_2, ed2[m]),
-                                    winding_scaled(ed1[m], z3_1, ez1[m], ed3[m]),
-                                    winding_scaled(ed2[m], z3_2, ez2[m], ed3[m]) };
+                int wq[3] = { 0, 0, 0 };
+                if (!smooth_warp) {
+                    wq[0] = winding_scaled(ed1[m], z2_1, z1_2, ed2[m]);
+                    wq[1] = winding_scaled(ed1[m], z3_1, ez1[m], ed3[m]);
+                    wq[2] = winding_scaled(ed2[m], z3_2, ez2[m], ed3[m]);
+                }
                 const unsigned long long site =
                     (unsigned long long)((long long)z * N * (long long)N + (long long)roff[my] + mx);
 #pragma unroll

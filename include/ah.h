@@ -262,7 +262,9 @@ ah_status ah_autotune(ah_sim *sim, int32_t trial_steps, int32_t *chosen);
  * step is left before its next diagnostic point or its end, so the grouping of
  * its steps, and its results, do not depend on the other lattices of the
  * batch.  Such a lattice holds a second Pi/E set (20 instead of 15 arrays of
- * N^3 floats).  Its results agree with one step per launch to FP32 rounding.
+ * N^3 floats); from side 512 on it is launched with its own two-step grid
+ * (the rounds of such a batch then run without a CUDA graph).  Its results
+ * agree with one step per launch to FP32 rounding.
  * The other lattices take one step per launch.  (Small lattices gain nothing
  * from pairs: the two-step tile writes 30 x 6 of its 32 x 8 sites.) */
 enum { AH_BATCH_AUTOTUNE = 1, AH_BATCH_NO_GRAPH = 2, AH_BATCH_TWO_STEP = 4 };

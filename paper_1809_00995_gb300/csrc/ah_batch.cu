@@ -48,6 +48,12 @@ constexpr int kZChunk2 = 256;      // planes per two-step work item (each also r
 // recomputation than they save in DRAM traffic (on GB300 two-step passes tie
 // single steps at 512^3 and win at 1024^3).
 constexpr int kPairMinN = 512;
+// Paired lattices of at least this side fill the GPU with their own two-step
+// grid (512^3: 3096 CTAs): they run the single-lattice two-step kernel, whose
+// pointers and coefficients are kernel parameters, instead of taking items of
+// the persistent batched pass (which stages them in shared memory; 16.66
+// against 15.47 ms per step at 1024^3).
+constexpr int kDirectMinN = 512;
 constexpr int kServerRound = 20;   // longest round of the server (admission latency bound)
 constexpr int kMaxBatchN = 1290;   // largest lattice side with 32-bit site indices (1290^3 < 2^31)
 
@@ -270,9 +276,14 @@ struct Engine {
             bs[i].cur = L.cur;
             bs[i].pe = L.pe;
         }
+        direct.clear();
         for (int i : order) {
             const int cnt = bl[i].tiles_x * bl[i].tiles_y * bl[i].nchunk;
             for (int k = 0; k < cnt; ++k) items.push_back(make_int2(i, k));
+            if (bl[i].pairs && lats[i]->N >= kDirectMinN) {
+                direct.push_back(lats[i]);           // its own grid launches, no items
+                continue;
+            }
             const int cnt2 = bl[i].tiles2_x * bl[i].tiles2_y * bl[i].nchunk2;
             for (int k = 0; k < cnt2; ++k) items2.push_back(make_int2(i, k));
         }
@@ -311,6 +322,28 @@ struct Engine {
         return e;
     }
     int n_paired = 0, n_unpaired = 0;   // loaded lattices stepped in pairs / one step at a time
+    std::vector<Lat *> direct;          // paired lattices run by the single-lattice two-step kernel
+
+    // The two-step pass p of the current round of the directly launched lattice
+    // L, from its host mirror (step, buffers, Pi/E set at the round's start).
+    cudaError_t launch_direct(const Lat &L, int p)
+    {
+        const int n = L.step + 2 * p, cur = L.cur ^ (p & 1), pe = L.pe ^ (p & 1), o = 1 - cur;
+        const Fields<float> &F = L.F;
+        float *const q0[5] = { F.pir, F.pii, F.el[0], F.el[1], F.el[2] };
+        float *const *q = pe ? F.spare : q0;
+        float *const *oq = pe ? q0 : F.spare;
+        View2<float> v;
+        v.phr = F.phr[cur]; v.phi = F.phi[cur];
+        v.th1 = F.th[cur][0]; v.th2 = F.th[cur][1]; v.th3 = F.th[cur][2];
+        v.pir = q[0]; v.pii = q[1]; v.e1 = q[2]; v.e2 = q[3]; v.e3 = q[4];
+        v.ophr = F.phr[o]; v.ophi = F.phi[o];
+        v.oth1 = F.th[o][0]; v.oth2 = F.th[o][1]; v.oth3 = F.th[o][2];
+        v.opir = oq[0]; v.opii = oq[1]; v.oe1 = oq[2]; v.oe2 = oq[3]; v.oe3 = oq[4];
+        launches += 1;
+        return launch_fused2_step(v, L.N, host_kick_coef32(L.cfg, n), host_kick_coef32(L.cfg, n + 1),
+                                  fused2_default_variant(), st);
+    }
 
     // The launches of a round of R batched steps (R: the fewest steps any
     // unfinished lattice has to its next stop).  One step per launch: R
@@ -327,7 +360,13 @@ struct Engine {
                                           mode);
             };
             for (int r = 0; r < R / 2; ++r) {
+                for (const Lat *L : direct) {
+                    cudaError_t e = launch_direct(*L, r);
+                    if (e != cudaSuccess) return e;
+                }
                 if (n_paired) {
+                    // the other paired lattices; its advance kernel moves every
+                    // paired lattice on, the directly launched ones included
                     cudaError_t e = launch_fused2_batch(shape2, d_lat, d_state, nlat_loaded, d_items2, d_nitems + 1,
                                                         d_counter, num_sms, st);
                     if (e != cudaSuccess) return e;
@@ -357,7 +396,9 @@ struct Engine {
         TraceRange tr("batch steps");
         if (R <= 0) return cudaSuccess;
         ++rounds;
-        if (!use_graph) return enqueue_steps(R);
+        // a directly launched lattice takes its pointers and coefficients as
+        // kernel parameters, which change from round to round: no graph then
+        if (!use_graph || !direct.empty()) return enqueue_steps(R);
         const long long before = launches;
         const int mix = (n_paired ? 1 : 0) + (n_unpaired ? 2 : 0);
         const auto key = std::make_tuple(two ? 1000 + 64 * mix + 16 * shape2 + shape : shape, R, nlat_loaded);

@@ -206,14 +206,17 @@ def test_batch_two_step_equals_one_step_per_launch():
 def test_batch_1024cubed_light_cone_windows():
     """A 1024^3 FP32 lattice (matter era, s = 1, seed 3: the configuration of the
     throughput target) run through the batched engine with AH_BATCH_TWO_STEP
-    (lattices of side >= 512 in pairs, the others one step per launch) and
-    autotuned shapes, beside two small lattices: after 20 steps three 16^3
-    windows (two across the periodic seam) equal the oracle's evolution of the
-    (16 + 2 * 20)^3 windows of the same initial lattice; the small lattices equal
-    the oracle whole."""
+    (lattices of side >= 512 in pairs, each launched with its own two-step grid)
+    and autotuned shapes, beside a small lattice stepped in pairs by the
+    persistent two-step pass and one stepped one step per launch: after 20 steps
+    three 16^3 windows (two across the periodic seam) equal the oracle's
+    evolution of the (16 + 2 * 20)^3 windows of the same initial lattice; the
+    small lattices equal the oracle whole."""
     N, k, b = 1024, 20, 16
     big = short_config(N, ah.AH_MATTER, 1.0, 3, k, diag_every=0)
-    small = [short_config(24, ah.AH_RADIATION, 0.0, 5, k, diag_every=0),
+    # the 24^3 lattice is paired too (batched two-step pass); the 13^3 one takes
+    # one step per launch and ends on an odd step
+    small = [short_config(24, ah.AH_RADIATION, 0.0, 5, k, diag_every=0, flags=ah.AH_FLAG_TWO_STEP),
              short_config(13, ah.AH_MATTER, 0.0, 6, k + 1, diag_every=0)]
     cfgs = [big] + small
     orgs = [(1016, 5, 1019), (300, 1010, 7), (511, 512, 640)]

@@ -217,6 +217,20 @@ def cpu_oracle_rate(wl, budget_s=12.0, M=48):
                         "(%.1f ms) weighted 1/%d" % (M, N, n, 1e3 * t_step, 1e3 * t_diag, diag_every)
 
 
+def cpu_oracle_rate_single_thread(wl, budget_s=8.0, M=32):
+    """The same measurement on one host core (a child process with OMP_NUM_THREADS=1,
+    so that the oracle's OpenMP runtime starts with one thread)."""
+    code = ("import json, bench; r, c, smp = bench.cpu_oracle_rate(%r, %r, %d); "
+            "print(json.dumps({'value': r, 'cores': c, 'sample': smp}))" % (wl, budget_s, M))
+    env = dict(os.environ, OMP_NUM_THREADS="1")
+    try:
+        out = subprocess.run([sys.executable, "-c", code], cwd=ROOT, env=env, capture_output=True, text=True,
+                             timeout=300)
+        return json.loads(out.stdout.strip().splitlines()[-1])
+    except Exception as e:                      # reported, not fatal: the main line still prints
+        return {"unavailable": str(e)[:200]}
+
+
 def batch_configs(ah, count=64, seed=4):
     """The batched-ensemble workload: N ~ U{64, 96, 128, 192, 256}, era ~ U{radiation,
     matter}, s ~ U{0, 1} from a fixed-seed host RNG, seeds 100..163, each run to
@@ -541,7 +555,8 @@ def main():
     cpu = None
     if rank == 0 and world == 1 and not a.no_cpu:
         rate, cores, sample = cpu_oracle_rate(wl)
-        cpu = {"value": rate, "unit": "site-updates/s", "cores": cores, "kind": "oracle", "sample": sample}
+        cpu = {"value": rate, "unit": "site-updates/s", "cores": cores, "kind": "oracle", "sample": sample,
+               "single_thread": cpu_oracle_rate_single_thread(wl)}
 
     if rank == 0:
         line = {

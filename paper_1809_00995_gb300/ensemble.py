@@ -83,16 +83,18 @@ def case_configs(ah, name, N, seeds, diag_every, seed0=1):
     return cfgs
 
 
-def scaling_ensemble(N=512, seeds=5, cases=tuple(CASES), diag_every=10, window=0.5):
-    """Run every case for `seeds` seeds (one batched job per case) and return the
-    per-run and per-case scaling quantities."""
+def scaling_ensemble(N=512, seeds=5, cases=tuple(CASES), diag_every=10, window=0.5, two_step=True):
+    """Run every case for `seeds` seeds (one batched job per case; with two_step,
+    AH_BATCH_TWO_STEP: lattices of side >= 512 two leapfrog steps per launch) and
+    return the per-run and per-case scaling quantities."""
     import paper_1809_00995_gb300 as ah
-    out = {"N": N, "seeds": seeds, "diag_every": diag_every, "window": window, "cases": {}}
+    out = {"N": N, "seeds": seeds, "diag_every": diag_every, "window": window, "two_step": two_step, "cases": {}}
     for name in cases:
         cfgs = case_configs(ah, name, N, seeds, diag_every)
         t0 = time.perf_counter()
         nsteps = max(int(round((c.tau_end - c.tau0) / c.dt)) for c in cfgs)
-        series, stats = ah.ah_batch_run(cfgs, series_cap=nsteps // diag_every + 2)
+        series, stats = ah.ah_batch_run(cfgs, flags=ah.AH_BATCH_TWO_STEP if two_step else 0,
+                                        series_cap=nsteps // diag_every + 2)
         wall = time.perf_counter() - t0
         try:
             runs = [run_scaling(ser, c.tau0, c.tau_end, window) for ser, c in zip(series, cfgs)]
@@ -126,8 +128,9 @@ def main():
     ap.add_argument("--window", type=float, default=0.5)
     ap.add_argument("--cases", default=",".join(CASES))
     ap.add_argument("--json", default=None, help="write the full result here")
+    ap.add_argument("--one-step", action="store_true", help="one leapfrog step per launch for every lattice")
     a = ap.parse_args()
-    res = scaling_ensemble(a.N, a.seeds, tuple(a.cases.split(",")), a.diag_every, a.window)
+    res = scaling_ensemble(a.N, a.seeds, tuple(a.cases.split(",")), a.diag_every, a.window, not a.one_step)
     print(table(res))
     for name, c in res["cases"].items():
         print("%s: %d runs, %.1f s, %.3g site-updates/s, tau_ref %.3g, tau_end %.3g"

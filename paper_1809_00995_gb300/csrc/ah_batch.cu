@@ -361,6 +361,10 @@ struct Engine {
             };
             for (int r = 0; r < R / 2; ++r) {
                 for (const Lat *L : direct) {
+                    // a lattice that has reached its end stays loaded until the
+                    // batch is done: it takes no more passes (an unfinished one
+                    // has at least R steps to its next stop and takes them all)
+                    if (L->step >= L->nsteps) continue;
                     cudaError_t e = launch_direct(*L, r);
                     if (e != cudaSuccess) return e;
                 }

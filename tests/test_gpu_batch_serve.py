@@ -234,6 +234,25 @@ def test_batch_1024cubed_light_cone_windows():
     assert o["step"] == k and o["n_sites"] == N ** 3 and o["nonfinite"] == 0 and o["gauss_rel"] < 1e-5
 
 
+def test_batch_large_paired_lattice_ending_before_the_others():
+    """A 512^3 lattice stepped in pairs with its own two-step grid (AH_BATCH_TWO_STEP)
+    ends after 10 steps while a small lattice runs on to 30: the rounds after its
+    end leave it alone, so its final state (an 8^3 window across the seam, against
+    the oracle's evolution of the (8 + 2 * 10)^3 window) and its observables are
+    those of step 10."""
+    N, k, b = 512, 10, 8
+    big = short_config(N, ah.AH_RADIATION, 0.0, 8, k, diag_every=0)
+    small = short_config(20, ah.AH_MATTER, 1.0, 9, 3 * k, diag_every=4)
+    org = (508, 250, 3)
+    series, _, fields = ah.ah_batch_run_ex([big, small], [(0, *org, b, b, b), (1, 0, 0, 0, 20, 20, 20)],
+                                           flags=ah.AH_BATCH_TWO_STEP, series_cap=16)
+    ref, _ = oracle_fields(big, k, M=b + 2 * k, origin=[(o - k) % N for o in org])
+    assert max(rel_err(fields[0], ref[:, k:k + b, k:k + b, k:k + b])) <= TOL32
+    ref_small, _ = oracle_fields(small, 3 * k)
+    assert max(rel_err(fields[1], ref_small)) <= TOL32
+    assert series[0][-1]["step"] == k and series[1][-1]["step"] == 3 * k
+
+
 def test_batch_window_arguments_are_checked():
     c = short_config(8, ah.AH_RADIATION, 0.0, 1, 2)
     for w in [(1, 0, 0, 0, 4, 4, 4), (0, 0, 0, 0, 9, 4, 4), (0, 0, 0, 0, 0, 4, 4)]:

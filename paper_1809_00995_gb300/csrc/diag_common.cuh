@@ -82,16 +82,6 @@ __device__ __forceinline__ int winding_scaled(C2<T> z1, C2<T> z2, C2<T> z3, C2<T
     if (near_cut(z1) | near_cut(z2) | near_cut(w3) | near_cut(w4) | near_cut(q4)) return INT_MIN;
     return carry(z1, z2, q2) + carry(q2, w3, q3) + carry(q3, w4, q4);
 }
-// True when every edge product has |Arg| < pi/4 with a relative margin (Re z >
-// 1.001 |Im z|): the signed sum of the four Args then lies in (-pi, pi), equals
-// Arg of the plaquette product, and the winding is 0 -- what both the carries
-// and the arctangent formula give.  A NaN (unscalable) edge fails the test.
-template <typename T>
-__device__ __forceinline__ bool small_args(C2<T> a, C2<T> b, C2<T> c, C2<T> d)
-{
-    const T k = T(1.001);
-    return (a.r > k * fabs(a.i)) & (b.r > k * fabs(b.i)) & (c.r > k * fabs(c.i)) & (d.r > k * fabs(d.i));
-}
 // The same from unscaled edge products.
 template <typename T>
 __device__ __forceinline__ int winding_carry(C2<T> z1, C2<T> z2, C2<T> z3, C2<T> z4)

@@ -275,6 +275,12 @@ __device__ __forceinline__ void fused_tile(const View<real> &v, int N, int zc, c
         // B: plaquette sines of plane z on the tile (own sites) and its low halos
         const cpx<real> *U0 = sU + bc * 3 * NE, *U1p = sU + bn * 3 * NE;
         real p12[NS], p13[NS], p23[NS];
+        [[maybe_unused]] Z ez1[NS], ez2[NS];      // MODE_DIAG: own d = 1, 2 edges of plane z+1
+        // MODE_DIAG: a plaquette whose four edges all have |Arg| < pi/4 has
+        // W = 0; when every edge that the CTA's plaquettes of plane z use passes
+        // that test (smooth regions), the carry chains are skipped
+        [[maybe_unused]] bool own_smooth = true;
+        [[maybe_unused]] auto smooth1 = [](const Z &z) { return z.r > real(1.001) * fabs(z.i); };
         [[maybe_unused]] real bcos[NS];          // MODE_DIAG: 1 - cos Xi summed over the three orientations
 #pragma unroll
         for (int m = 0; m < NS; ++m) {
@@ -304,18 +310,26 @@ __device__ __forceinline__ void fused_tile(const View<real> &v, int N, int zc, c
             for (int m = 0; m < NS; ++m) {
                 const int e = eix(m);
                 ed3[m] = edge(F0[e], U0[2 * NE + e], ph_p[m]);
+                ez1[m] = edge(F1[e], U1p[e], F1[e + 1]);
+                ez2[m] = edge(F1[e], U1p[NE + e], F1[e + EX]);
                 sE[e] = ed1[m];
                 sE[NE + e] = ed2[m];
                 sE[2 * NE + e] = ed3[m];
+                own_smooth = own_smooth && smooth1(ed1[m]) && smooth1(ed2[m]) && smooth1(ed3[m]) &&
+                             smooth1(ez1[m]) && smooth1(ez2[m]);
             }
             if (tid < TY) {
                 const int e = (tid + 1) * EX + EX - 1;
-                sE[NE + e] = edge(F0[e], U0[NE + e], F0[e + EX]);
-                sE[2 * NE + e] = edge(F0[e], U0[2 * NE + e], F1[e]);
+                const Z a = edge(F0[e], U0[NE + e], F0[e + EX]), b = edge(F0[e], U0[2 * NE + e], F1[e]);
+                sE[NE + e] = a;
+                sE[2 * NE + e] = b;
+                own_smooth = own_smooth && smooth1(a) && smooth1(b);
             } else if (tid < TY + TX) {
                 const int e = (EY - 1) * EX + tid - TY + 1;
-                sE[e] = edge(F0[e], U0[e], F0[e + 1]);
-                sE[2 * NE + e] = edge(F0[e], U0[2 * NE + e], F1[e]);
+                const Z a = edge(F0[e], U0[e], F0[e + 1]), b = edge(F0[e], U0[2 * NE + e], F1[e]);
+                sE[e] = a;
+                sE[2 * NE + e] = b;
+                own_smooth = own_smooth && smooth1(a) && smooth1(b);
             }
         }
         if (STEP && tid < G::NPHALO) {
@@ -325,7 +339,9 @@ __device__ __forceinline__ void fused_tile(const View<real> &v, int N, int zc, c
             sP[G::NP + p] = plaq(U0[e], U0[2 * NE + e + 1], U1p[e], U0[2 * NE + e]);
             sP[2 * G::NP + p] = plaq(U0[NE + e], U0[2 * NE + e + EX], U1p[NE + e], U0[2 * NE + e]);
         }
-        __syncthreads();
+        [[maybe_unused]] bool smooth_cta = false;
+        if constexpr (DIAG) smooth_cta = __syncthreads_and(own_smooth) != 0;
+        else __syncthreads();
 
         // C: kicks and drifts of the own sites of plane z
         const cpx<real> *F0 = sF + bc * NE;
@@ -358,23 +374,6 @@ __device__ __forceinline__ void fused_tile(const View<real> &v, int N, int zc, c
             const real ne1 = c.c_edamp * e1[m] + c.c_cur * cu1 - c.c_curl * cl1;
             const real ne2 = c.c_edamp * e2[m] + c.c_cur * cu2 - c.c_curl * cl2;
             const real ne3 = c.c_edamp * e3[m] + c.c_cur * cu3 - c.c_curl * cl3;
-            [[maybe_unused]] Z ez1[NS], ez2[NS];   // MODE_DIAG: own d = 1, 2 edges of plane z+1
-            if constexpr (DIAG) {
-                const cpx<real> *F1 = sF + bn * NE;
-                ez1[m] = edge(F1[e], U1p[e], F1[e + 1]);
-                ez2[m] = edge(F1[e], U1p[NE + e], F1[e + EX]);
-            }
-            // MODE_DIAG: a plaquette whose four edges all have |Arg| < pi/4
-            // has W = 0; where that holds for the three plaquettes of every
-            // site of the warp, as in smooth regions, the carry chains are
-            // skipped (the vote is taken with the whole warp converged)
-            [[maybe_unused]] bool smooth_warp = false;
-            if constexpr (DIAG) {
-                const Z a21 = sE[NE + e + 1], a31 = sE[2 * NE + e + 1], a12 = sE[e + EX], a32 = sE[2 * NE + e + EX];
-                smooth_warp = __all_sync(0xffffffffu, small_args(ed1[m], a21, a12, ed2[m]) &
-                                                          small_args(ed1[m], a31, ez1[m], ed3[m]) &
-                                                          small_args(ed2[m], a32, ez2[m], ed3[m]));
-            }
             if constexpr (DIAG) if (wr[m / RX]) {
                 const real K = pr[m] * pr[m] + pim[m] * pim[m];
                 const real d1r = w1.r - f0.r, d1i = w1.i - f0.i, d2r = w2.r - f0.r, d2i = w2.i - f0.i;
@@ -432,7 +431,7 @@ __device__ __forceinline__ void fused_tile(const View<real> &v, int N, int zc, c
                 const Z z2_1 = sE[NE + e + 1], z3_1 = sE[2 * NE + e + 1];
                 const Z z1_2 = sE[e + EX], z3_2 = sE[2 * NE + e + EX];
                 int wq[3] = { 0, 0, 0 };
-                if (!smooth_warp) {
+                if (!smooth_cta) {
                     wq[0] = winding_scaled(ed1[m], z2_1, z1_2, ed2[m]);
                     wq[1] = winding_scaled(ed1[m], z3_1, ez1[m], ed3[m]);
                     wq[2] = winding_scaled(ed2[m], z3_2, ez2[m], ed3[m]);

@@ -576,6 +576,8 @@ def main():
                     "d2h_bytes_per_step": d2h, "h2d_bytes_per_job": ctypes.sizeof(ah.ah_config),
                     "timed": "ah_create_ex + %d x (ah_step(%d) + ah_observables to host) + ah_destroy, host clock"
                              % (a.steps, diag_every)},
+            # per bench step: the step launches and the diagnostics pass (tile
+            # walk, ordered sum, near-cut fix-up)
             "gpu_launches": a.steps * (diag_every * info["step_launches"] // steps_per_launch + 3),
             "batch": batch,
             "batch1024": batch1024,

@@ -192,6 +192,22 @@ ah_status ah_observables(ah_sim *sim, ah_obs *out);
 ah_status ah_observables_box(ah_sim *sim, int32_t x0, int32_t y0, int32_t z0,
                              int32_t nx, int32_t ny, int32_t nz, ah_obs *out);
 
+/* Asynchronous observables of the current state (the quantities of
+ * ah_observables, Sec. 2).  ah_observables_start enqueues the whole-lattice
+ * diagnostics pass on a second stream of the simulation and returns without
+ * waiting; the pass reads the state as it is at the call (the snapshot), and a
+ * list overflow of near-cut plaquettes is settled on the device (all windings
+ * counted again in FP64).  Later ah_step calls go on: each launch that would
+ * overwrite the snapshot first waits for the pass; in two-step mode the first
+ * two-step launch after the start writes the other buffer set and runs
+ * alongside the pass.  ah_observables_finish waits for the pass and fills
+ * *out for the step of the snapshot (status as ah_observables).  One pass at a
+ * time per simulation: a second start, ah_observables, ah_observables_box and
+ * ah_autotune return AH_ERR_BUSY while one is pending; ah_set_fields and
+ * ah_set_stream wait for it. */
+ah_status ah_observables_start(ah_sim *sim);
+ah_status ah_observables_finish(ah_sim *sim, ah_obs *out);
+
 /* Copy the state of the window [x0, x0+nx) x ... (mod N) to host memory `out`
  * as FP64: 10 components, each nz*ny*nx with x fastest (10*nx*ny*nz doubles).
  * Waits for the simulation's stream. */

@@ -102,6 +102,8 @@ _SIGS = {
     "ah_create_ex": ([ctypes.POINTER(ah_config), ctypes.POINTER(ctypes.c_void_p)], ctypes.c_int),
     "ah_step": ([ctypes.c_void_p, ctypes.c_int64], ctypes.c_int),
     "ah_observables": ([ctypes.c_void_p, ctypes.POINTER(ah_obs)], ctypes.c_int),
+    "ah_observables_start": ([ctypes.c_void_p], ctypes.c_int),
+    "ah_observables_finish": ([ctypes.c_void_p, ctypes.POINTER(ah_obs)], ctypes.c_int),
     "ah_observables_box": ([ctypes.c_void_p] + [ctypes.c_int32] * 6 + [ctypes.POINTER(ah_obs)], ctypes.c_int),
     "ah_get_fields": ([ctypes.c_void_p] + [ctypes.c_int32] * 6 + [ctypes.c_void_p], ctypes.c_int),
     "ah_set_fields": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64], ctypes.c_int),
@@ -201,6 +203,18 @@ def ah_step(h, nsteps: int):
 def ah_observables(h, check_finite: bool = True) -> dict:
     o = ah_obs()
     st = load().ah_observables(h, ctypes.byref(o))
+    if st != AH_OK and not (st == AH_ERR_NONFINITE and not check_finite):
+        _check(st)
+    return o.as_dict()
+
+
+def ah_observables_start(h):
+    _check(load().ah_observables_start(h))
+
+
+def ah_observables_finish(h, check_finite: bool = True) -> dict:
+    o = ah_obs()
+    st = load().ah_observables_finish(h, ctypes.byref(o))
     if st != AH_OK and not (st == AH_ERR_NONFINITE and not check_finite):
         _check(st)
     return o.as_dict()
@@ -411,6 +425,13 @@ class Sim:
 
     def observables(self, check_finite=True) -> dict:
         return ah_observables(self.h, check_finite)
+
+    def observables_start(self):
+        ah_observables_start(self.h)
+        return self
+
+    def observables_finish(self, check_finite=True) -> dict:
+        return ah_observables_finish(self.h, check_finite)
 
     def observables_box(self, x0, y0, z0, nx, ny, nz) -> dict:
         return ah_observables_box(self.h, x0, y0, z0, nx, ny, nz)

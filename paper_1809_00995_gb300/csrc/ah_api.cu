@@ -143,6 +143,16 @@ struct ah_sim {
     int tma_drop_q;             // fault injection: Pi/E plane whose copy is never issued (-1: none)
     cudaStream_t stream;
     bool own_stream;
+    // asynchronous observables (ah_observables_start / _finish): the pass runs
+    // on aux after ev_snap; ev_done marks its end.  Until the main stream has
+    // waited for ev_done (diag_fenced), a launch that would overwrite the
+    // snapshot must wait first; in two-step mode the first two-step launch
+    // after the start writes the other buffer set and may run alongside.
+    cudaStream_t aux;
+    cudaEvent_t ev_snap, ev_done;
+    bool diag_pending, diag_fenced;
+    int diag_free_pairs;
+    int64_t diag_step;
 };
 
 namespace {
@@ -266,6 +276,17 @@ const char *variant_name(const ah_sim *h, int v)
     case 2: return kTmaShapes[i].name;
     default: return fused_variant_name<float>(v);
     }
+}
+
+// Make the simulation's stream wait for a pending asynchronous observables
+// pass before work that would change its snapshot.
+ah_status diag_fence(ah_sim *h)
+{
+    if (h->diag_pending && !h->diag_fenced) {
+        AH_CUDA(cudaStreamWaitEvent(h->stream, h->ev_done, 0));
+        h->diag_fenced = true;
+    }
+    return AH_OK;
 }
 
 template <typename real>
@@ -457,9 +478,37 @@ ah_status host_validate(const ah_config &c) { return validate(c); }
 ah_status host_fail(ah_status st, const char *msg) { return fail(st, "%s", msg); }
 }  // namespace ah
 
+namespace {
+template <typename real>
+ah_status diag_start(ah_sim *h)
+{
+    Fields<real> &F = *(Fields<real> *)(h->cfg.precision == AH_FP32 ? (void *)&h->f32 : (void *)&h->f64);
+    const DiagCoef dc = diag_coef(h->cfg, h->step);
+    const View<real> v = make_view(F, h->cur, false);
+    const int N = h->N;
+    AH_CUDA(cudaEventRecord(h->ev_snap, h->stream));
+    AH_CUDA(cudaStreamWaitEvent(h->aux, h->ev_snap, 0));
+    if (h->cfg.flags & AH_FLAG_EXACT_DIAG) {
+        AH_CUDA(launch_diag<real>(v, N, Box{ 0, 0, 0, N, N, N }, dc, h->partials, h->diag_blocks, h->result, h->list,
+                                  true, h->aux));
+    } else {
+        if (fused_diag_ctas(N) > h->nparts)
+            return fail(AH_ERR_CUDA, "diagnostics scratch too small: the N=%d pass needs %d partials, %d allocated", N,
+                        fused_diag_ctas(N), h->nparts);
+        AH_CUDA(launch_diag_whole<real>(v, N, dc, h->partials, h->nparts, h->result, h->list, h->diag_blocks, h->aux));
+        // a list overflow is settled on the device: the snapshot may change
+        // before the host could look at the count
+        AH_CUDA(launch_wind_recount_on_overflow<real>(v, N, h->list, h->result, h->diag_blocks, h->aux));
+    }
+    AH_CUDA(cudaMemcpyAsync(h->host_result, h->result, sizeof(DiagPartial), cudaMemcpyDeviceToHost, h->aux));
+    AH_CUDA(cudaEventRecord(h->ev_done, h->aux));
+    return AH_OK;
+}
+}  // namespace
+
 extern "C" {
 
-int ah_abi_version(void) { return 3; }
+int ah_abi_version(void) { return 4; }
 
 const char *ah_last_error(void) { return g_err.c_str(); }
 
@@ -605,10 +654,15 @@ ah_status ah_step(ah_sim *h, int64_t nsteps)
     int64_t q = 0;
     if (h->two_step) {
         for (; q + 2 <= nsteps; q += 2) {
+            // the first pass after an asynchronous observables start reads the
+            // snapshot and writes the other set: it may overlap the pass
+            if (h->diag_pending && !h->diag_fenced && h->diag_free_pairs > 0) --h->diag_free_pairs;
+            else if ((st = diag_fence(h)) != AH_OK) return st;
             if ((st = do_step2(h, h->step)) != AH_OK) return st;
             h->step += 2;
         }
     }
+    if (q < nsteps && (st = diag_fence(h)) != AH_OK) return st;
     for (; q < nsteps; ++q) {
         st = h->cfg.precision == AH_FP32 ? do_step<float>(h, h->step) : do_step<double>(h, h->step);
         if (st != AH_OK) return st;
@@ -624,6 +678,8 @@ ah_status ah_observables_box(ah_sim *h, int32_t x0, int32_t y0, int32_t z0, int3
     ah_status st = enter(h);
     if (st != AH_OK) return st;
     if (!out) return fail(AH_ERR_ARG, "null output");
+    if (h->diag_pending)
+        return fail(AH_ERR_BUSY, "an asynchronous observables pass is pending: call ah_observables_finish first");
     const int N = h->N;
     if (nx < 1 || ny < 1 || nz < 1 || nx > N || ny > N || nz > N)
         return fail(AH_ERR_ARG, "box extent must be in [1, N]");
@@ -636,6 +692,42 @@ ah_status ah_observables(ah_sim *h, ah_obs *out)
 {
     if (!h) return fail(AH_ERR_ARG, "null simulation handle");
     return ah_observables_box(h, 0, 0, 0, h->N, h->N, h->N, out);
+}
+
+ah_status ah_observables_start(ah_sim *h)
+{
+    TraceRange tr("ah_observables_start");
+    ah_status st = enter(h);
+    if (st != AH_OK) return st;
+    if (h->diag_pending) return fail(AH_ERR_BUSY, "an asynchronous observables pass is already pending");
+    if (!h->aux) {
+        AH_CUDA(cudaStreamCreateWithFlags(&h->aux, cudaStreamNonBlocking));
+        AH_CUDA(cudaEventCreateWithFlags(&h->ev_snap, cudaEventDisableTiming));
+        AH_CUDA(cudaEventCreateWithFlags(&h->ev_done, cudaEventDisableTiming));
+    }
+    st = h->cfg.precision == AH_FP32 ? diag_start<float>(h) : diag_start<double>(h);
+    if (st != AH_OK) return st;
+    h->diag_pending = true;
+    h->diag_fenced = false;
+    h->diag_free_pairs = h->two_step ? 1 : 0;
+    h->diag_step = h->step;
+    return AH_OK;
+}
+
+ah_status ah_observables_finish(ah_sim *h, ah_obs *out)
+{
+    TraceRange tr("ah_observables_finish");
+    ah_status st = enter(h);
+    if (st != AH_OK) return st;
+    if (!out) return fail(AH_ERR_ARG, "null output");
+    if (!h->diag_pending) return fail(AH_ERR_ARG, "no asynchronous observables pass was started");
+    const cudaError_t e = cudaEventSynchronize(h->ev_done);
+    h->diag_pending = false;
+    if (e != cudaSuccess) return fail(AH_ERR_CUDA, "asynchronous observables: %s", cudaGetErrorString(e));
+    fill_obs(h->cfg, h->diag_step, h->nsites, *h->host_result, out);
+    if (out->nonfinite)
+        return fail(AH_ERR_NONFINITE, "%lld sites have non-finite diagnostics", (long long)out->nonfinite);
+    return AH_OK;
 }
 
 ah_status ah_get_fields(ah_sim *h, int32_t x0, int32_t y0, int32_t z0, int32_t nx, int32_t ny, int32_t nz,
@@ -667,6 +759,7 @@ ah_status ah_set_fields(ah_sim *h, const double *in, int64_t step)
     ah_status st = enter(h);
     if (st != AH_OK) return st;
     if (!in || step < 0) return fail(AH_ERR_ARG, "null input or negative step");
+    if ((st = diag_fence(h)) != AH_OK) return st;
     const size_t bytes = sizeof(double) * 10 * (size_t)h->nsites;
     double *tmp = nullptr;
     AH_CUDA(cudaMalloc(&tmp, bytes));
@@ -686,6 +779,8 @@ ah_status ah_set_stream(ah_sim *h, void *stream)
 {
     ah_status st = enter(h);
     if (st != AH_OK) return st;
+    if (h->diag_pending) AH_CUDA(cudaEventSynchronize(h->ev_done));
+    h->diag_fenced = h->diag_pending;         // the pass has ended: no later work need wait
     AH_CUDA(cudaStreamSynchronize(h->stream));
     if (stream) {
         if (h->own_stream) cudaStreamDestroy(h->stream);
@@ -749,6 +844,7 @@ ah_status ah_autotune(ah_sim *h, int32_t trial_steps, int32_t *chosen)
     ah_status st = enter(h);
     if (st != AH_OK) return st;
     if (!h->pristine) return fail(AH_ERR_BUSY, "autotune needs the freshly created state");
+    if (h->diag_pending) return fail(AH_ERR_BUSY, "an asynchronous observables pass is pending");
     if (trial_steps < 1) return fail(AH_ERR_ARG, "trial_steps must be >= 1");
     if (h->cfg.kernel == AH_KERNEL_PLAIN) {
         if (chosen) *chosen = h->variant;
@@ -799,6 +895,12 @@ void ah_destroy(ah_sim *h)
     if (!h) return;
     cudaSetDevice(h->device);
     if (h->stream) cudaStreamSynchronize(h->stream);
+    if (h->aux) {
+        cudaStreamSynchronize(h->aux);
+        cudaStreamDestroy(h->aux);
+    }
+    if (h->ev_snap) cudaEventDestroy(h->ev_snap);
+    if (h->ev_done) cudaEventDestroy(h->ev_done);
     if (h->dmem) cudaFree(h->dmem);
     if (h->partials) cudaFree(h->partials);
     if (h->list.count) cudaFree(h->list.count);

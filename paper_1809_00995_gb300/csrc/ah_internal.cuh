@@ -163,6 +163,12 @@ cudaError_t launch_diag(const View<real> &v, int N, Box b, const DiagCoef &c,
 
 int diag_grid_blocks(int num_sms);
 
+// If the near-cut list of a pass overflowed (checked on the device), clear the
+// winding counters of *result and count every plaquette again in FP64.
+template <typename real>
+cudaError_t launch_wind_recount_on_overflow(const View<real> &v, int N, DiagList list, DiagPartial *result,
+                                            int nblocks, cudaStream_t st);
+
 // Whole-lattice diagnostics through the fused step's tile walk (tile 32 x 8,
 // nothing written back): one DiagPartial per CTA of the grid that
 // fused_diag_grid gives (fused_diag_ctas of them), near-cut plaquettes

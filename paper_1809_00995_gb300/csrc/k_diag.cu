@@ -495,7 +495,9 @@ __global__ void k_noalloc_fixup(View<real> v, int N, DiagList list, DiagPartial 
     }
 }
 
-// On list overflow: clear the winding counters ...
+// On list overflow (here and in the asynchronous observables pass, where the
+// host cannot decide before the snapshot may change): clear the winding
+// counters ...
 __global__ void k_noalloc_wind_clear(DiagList list, DiagPartial *result)
 {
     if (*list.count <= (unsigned long long)list.capacity) return;
@@ -524,6 +526,19 @@ __global__ void k_noalloc_wind_all(View<real> v, int N, DiagList list, DiagParti
 }
 
 }  // namespace
+
+template <typename real>
+cudaError_t launch_wind_recount_on_overflow(const View<real> &v, int N, DiagList list, DiagPartial *result,
+                                            int nblocks, cudaStream_t st)
+{
+    k_noalloc_wind_clear<<<1, 32, 0, st>>>(list, result);
+    k_noalloc_wind_all<real><<<nblocks, 256, 0, st>>>(v, N, list, result);
+    return cudaGetLastError();
+}
+template cudaError_t launch_wind_recount_on_overflow<float>(const View<float> &, int, DiagList, DiagPartial *, int,
+                                                            cudaStream_t);
+template cudaError_t launch_wind_recount_on_overflow<double>(const View<double> &, int, DiagList, DiagPartial *, int,
+                                                             cudaStream_t);
 
 }  // namespace ah
 

@@ -321,6 +321,32 @@ def test_server_results_same_alone_and_in_the_mix(pairs):
             close_obs(obs, single_series(c)[-1])
 
 
+def test_server_large_paired_request_matches_oracle():
+    """A 512^3 request stepped in pairs (AH_BATCH_TWO_STEP server: its own two-step
+    grid, launched from the server's copy of its state) served beside small
+    requests of other lengths: its final fields (an 8^3 window across the seam,
+    against the oracle's (8 + 2 * 12)^3 window) and the small ones' equal the
+    oracle's."""
+    N, k, b = 512, 12, 8
+    big = short_config(N, ah.AH_MATTER, 1.0, 21, k, diag_every=0)
+    smalls = [short_config(16, ah.AH_RADIATION, 0.0, 22, 2 * k + 1, diag_every=5),
+              short_config(20, ah.AH_MATTER, 0.0, 23, 7, diag_every=0)]
+    org = (505, 0, 300)
+    with ah.Server(hbm_budget_bytes=24 << 30, max_slots=4, flags=ah.AH_BATCH_TWO_STEP) as srv:
+        bid, (bf,) = srv.submit_ex(big, [(*org, b, b, b)])
+        sids = [srv.submit_ex(c, [(0, 0, 0, c.N, c.N, c.N)]) for c in smalls]
+        bobs, _, _ = wait_done(srv, bid)
+        for (rid, (f,)), c in zip(sids, smalls):
+            obs, _, _ = wait_done(srv, rid)
+            n = int(round((c.tau_end - c.tau0) / c.dt))
+            ref, _ = oracle_fields(c, n)
+            assert max(rel_err(f, ref)) <= TOL32, c.N
+            assert obs["step"] == n
+    assert bobs["step"] == k
+    ref, _ = oracle_fields(big, k, M=b + 2 * k, origin=[(o - k) % N for o in org])
+    assert max(rel_err(bf, ref[:, k:k + b, k:k + b, k:k + b])) <= TOL32
+
+
 def test_server_budget_and_cancel():
     with ah.Server(hbm_budget_bytes=64 << 20, max_slots=4) as srv:
         with pytest.raises(ah.AhError) as e:

@@ -68,7 +68,7 @@ enum { AH_KERNEL_AUTO = 0, AH_KERNEL_PLAIN = 1, AH_KERNEL_FUSED = 2 };
  *  sign carries that equal the FP64 arctangent formula, with the plaquettes
  *  near a branch cut re-evaluated in FP64. */
 enum { AH_FLAG_EXACT_DIAG = 1, AH_FLAG_AUTOTUNE = 2, AH_FLAG_WRAP_THETA = 4, AH_FLAG_CORE_GROWTH = 8,
-       AH_FLAG_TWO_STEP = 16 };
+       AH_FLAG_TWO_STEP = 16, AH_FLAG_FUSED_DIAG = 32 };
 /* AUTOTUNE: at creation, time every compile-time shape of the fused step on
  * the initial state (then re-initialise it) and keep the fastest; results are
  * cached per (device, N, precision, two-step mode) for the life of the process.
@@ -95,7 +95,15 @@ enum { AH_FLAG_EXACT_DIAG = 1, AH_FLAG_AUTOTUNE = 2, AH_FLAG_WRAP_THETA = 4, AH_
  * mode ah_set_variant, ah_autotune and ah_info.variant / n_variants /
  * variant_name refer to the two-step shapes, and the TMA-fed single-step
  * shapes are not available.  Refused (AH_ERR_ARG) for FP64 and for
- * AH_KERNEL_PLAIN. */
+ * AH_KERNEL_PLAIN.
+ * FUSED_DIAG (with TWO_STEP only, else AH_ERR_ARG): an asynchronous
+ * observables pass (ah_observables_start) is always taken by the next
+ * two-step launch, which reads the state of the pass for its first step
+ * anyway (see ah_observables_start).  Without the flag a two-step simulation
+ * chooses by the last whole-lattice observables it returned: the fused launch
+ * when fewer than 1e-3 of the plaquettes were pierced (a string network in an
+ * otherwise smooth field, where most tiles skip the winding carries), else a
+ * separate pass.  No effect in batches and the server. */
 
 typedef struct ah_config {
     int32_t N;            /* lattice side, 4 <= N <= 2048                         */
@@ -200,11 +208,19 @@ ah_status ah_observables_box(ah_sim *sim, int32_t x0, int32_t y0, int32_t z0,
  * counted again in FP64).  Later ah_step calls go on: each launch that would
  * overwrite the snapshot first waits for the pass; in two-step mode the first
  * two-step launch after the start writes the other buffer set and runs
- * alongside the pass.  ah_observables_finish waits for the pass and fills
- * *out for the step of the snapshot (status as ah_observables).  One pass at a
- * time per simulation: a second start, ah_observables, ah_observables_box and
- * ah_autotune return AH_ERR_BUSY while one is pending; ah_set_fields and
- * ah_set_stream wait for it. */
+ * alongside the pass.  A two-step simulation may instead defer the pass (see
+ * AH_FLAG_FUSED_DIAG): then the next ah_step of two or more steps runs its
+ * first two steps with the diagnostics of the snapshot folded in (one kernel
+ * pass over the state instead of two; the steps are those of the plain
+ * two-step pass, bit for bit), and the pass runs on its own if
+ * ah_observables_finish, ah_set_fields or a single step comes first.  The sums
+ * then differ from those of ah_observables by the summation order only (a few
+ * 1e-7 relative); windings, max |G| and max |theta| are the same.
+ * ah_observables_finish waits for the pass and fills *out for the step of the
+ * snapshot (status as ah_observables).  One pass at a time per simulation: a
+ * second start, ah_observables, ah_observables_box and ah_autotune return
+ * AH_ERR_BUSY while one is pending; ah_set_fields and ah_set_stream wait for
+ * it. */
 ah_status ah_observables_start(ah_sim *sim);
 ah_status ah_observables_finish(ah_sim *sim, ah_obs *out);
 
@@ -244,6 +260,8 @@ typedef struct ah_info {
     int32_t variant;         /* shape of the fused step in use             */
     int32_t n_variants;      /* shapes available for this precision        */
     char variant_name[32];
+    int64_t fused_diag_passes;   /* observables passes taken by two-step
+                                    launches so far (AH_FLAG_FUSED_DIAG)   */
 } ah_info;
 ah_status ah_get_info(const ah_sim *sim, ah_info *out);
 

@@ -27,6 +27,7 @@ AH_MINKOWSKI, AH_RADIATION, AH_MATTER = 0, 1, 2
 AH_FP32, AH_FP64 = 0, 1
 AH_KERNEL_AUTO, AH_KERNEL_PLAIN, AH_KERNEL_FUSED = 0, 1, 2
 AH_FLAG_EXACT_DIAG, AH_FLAG_AUTOTUNE, AH_FLAG_WRAP_THETA, AH_FLAG_CORE_GROWTH, AH_FLAG_TWO_STEP = 1, 2, 4, 8, 16
+AH_FLAG_FUSED_DIAG = 32
 AH_BATCH_AUTOTUNE, AH_BATCH_NO_GRAPH, AH_BATCH_TWO_STEP = 1, 2, 4
 
 SUM_NAMES = ("L", "rho", "p", "K", "G2", "V", "Eel", "B", "KV", "G2V", "KL", "G2L", "pL", "rhoL",
@@ -90,7 +91,7 @@ class ah_info(ctypes.Structure):
     _fields_ = [("N", ctypes.c_int64), ("n_sites", ctypes.c_int64), ("precision", ctypes.c_int32),
                 ("kernel", ctypes.c_int32), ("state_bytes", ctypes.c_int64), ("step_bytes", ctypes.c_int64),
                 ("step_launches", ctypes.c_int64), ("variant", ctypes.c_int32), ("n_variants", ctypes.c_int32),
-                ("variant_name", ctypes.c_char * 32)]
+                ("variant_name", ctypes.c_char * 32), ("fused_diag_passes", ctypes.c_int64)]
 
 
 _SIGS = {

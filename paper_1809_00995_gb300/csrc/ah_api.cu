@@ -148,14 +148,25 @@ struct ah_sim {
     // waited for ev_done (diag_fenced), a launch that would overwrite the
     // snapshot must wait first; in two-step mode the first two-step launch
     // after the start writes the other buffer set and may run alongside.
+    // FP32 two-step simulations defer the pass instead (diag_deferred): the
+    // next two-step launch takes it (k_fused2_diag on the main stream, ev_done
+    // recorded there), or, if other work comes first, it runs on its own then.
     cudaStream_t aux;
     cudaEvent_t ev_snap, ev_done;
-    bool diag_pending, diag_fenced;
+    bool diag_pending, diag_fenced, diag_deferred;
+    int64_t fused_diag_passes;
+    // fraction of the plaquettes pierced at the last whole-lattice observables
+    // (1 before any): picks the fused or the separate pass for a deferral
+    double pierced_frac;
     int diag_free_pairs;
     int64_t diag_step;
 };
 
 namespace {
+
+// Largest fraction of pierced plaquettes at which a deferred observables pass
+// rides on the next two-step launch (k_fused2_diag) without AH_FLAG_FUSED_DIAG.
+constexpr double kFusedDiagPierced = 1e-3;
 
 template <typename real>
 void carve(Fields<real> &F, char *base, size_t n, bool spare = false)
@@ -202,8 +213,10 @@ ah_status validate(const ah_config &c)
     if (c.kernel < AH_KERNEL_AUTO || c.kernel > AH_KERNEL_FUSED)
         return fail(AH_ERR_ARG, "unknown kernel %d", c.kernel);
     if (c.flags & ~(AH_FLAG_EXACT_DIAG | AH_FLAG_AUTOTUNE | AH_FLAG_WRAP_THETA | AH_FLAG_CORE_GROWTH |
-                    AH_FLAG_TWO_STEP))
+                    AH_FLAG_TWO_STEP | AH_FLAG_FUSED_DIAG))
         return fail(AH_ERR_ARG, "unknown flags 0x%x", c.flags);
+    if ((c.flags & AH_FLAG_FUSED_DIAG) && !(c.flags & AH_FLAG_TWO_STEP))
+        return fail(AH_ERR_ARG, "AH_FLAG_FUSED_DIAG needs AH_FLAG_TWO_STEP");
     if ((c.flags & AH_FLAG_TWO_STEP) && (c.precision != AH_FP32 || c.kernel == AH_KERNEL_PLAIN))
         return fail(AH_ERR_ARG, "AH_FLAG_TWO_STEP needs FP32 and the fused kernel");
     if (!std::isfinite(c.s)) return fail(AH_ERR_ARG, "s must be finite");
@@ -278,10 +291,27 @@ const char *variant_name(const ah_sim *h, int v)
     }
 }
 
+template <typename real>
+ah_status diag_start(ah_sim *h);
+
+// A deferred observables pass that no two-step launch took: run it on its own
+// now (on aux, from the current state, which is still its snapshot).
+ah_status diag_undefer(ah_sim *h)
+{
+    if (!h->diag_deferred) return AH_OK;
+    h->diag_deferred = false;
+    const ah_status st = diag_start<float>(h);
+    if (st != AH_OK) return st;
+    h->diag_fenced = false;
+    h->diag_free_pairs = 0;
+    return AH_OK;
+}
+
 // Make the simulation's stream wait for a pending asynchronous observables
 // pass before work that would change its snapshot.
 ah_status diag_fence(ah_sim *h)
 {
+    if (ah_status st = diag_undefer(h); st != AH_OK) return st;
     if (h->diag_pending && !h->diag_fenced) {
         AH_CUDA(cudaStreamWaitEvent(h->stream, h->ev_done, 0));
         h->diag_fenced = true;
@@ -317,7 +347,7 @@ ah_status do_step(ah_sim *h, int64_t n)
 // Steps n and n + 1 in one pass (AH_FLAG_TWO_STEP): phi, theta go to the
 // other ping-pong buffer, Pi and E to the spare set, which then becomes the
 // current one.
-ah_status do_step2(ah_sim *h, int64_t n)
+View2<float> step2_view(ah_sim *h)
 {
     Fields<float> &F = h->f32;
     View2<float> v;
@@ -328,12 +358,46 @@ ah_status do_step2(ah_sim *h, int64_t n)
     v.ophr = F.phr[o]; v.ophi = F.phi[o];
     v.oth1 = F.th[o][0]; v.oth2 = F.th[o][1]; v.oth3 = F.th[o][2];
     v.opir = F.spare[0]; v.opii = F.spare[1]; v.oe1 = F.spare[2]; v.oe2 = F.spare[3]; v.oe3 = F.spare[4];
-    AH_CUDA(launch_fused2_step(v, h->N, kick_coef<float>(h->cfg, n), kick_coef<float>(h->cfg, n + 1), h->variant2,
-                               h->stream));
-    h->cur = o;
+    return v;
+}
+void step2_swap(ah_sim *h)
+{
+    Fields<float> &F = h->f32;
+    h->cur = 1 - h->cur;
     std::swap(F.pir, F.spare[0]);
     std::swap(F.pii, F.spare[1]);
     for (int d = 0; d < 3; ++d) std::swap(F.el[d], F.spare[2 + d]);
+}
+ah_status do_step2(ah_sim *h, int64_t n)
+{
+    AH_CUDA(launch_fused2_step(step2_view(h), h->N, kick_coef<float>(h->cfg, n), kick_coef<float>(h->cfg, n + 1),
+                               h->variant2, h->stream));
+    step2_swap(h);
+    return AH_OK;
+}
+// The same pass taking the deferred observables of the state n on the way:
+// partial sums, then (on the state n, which the pass leaves in place) the
+// FP64 windings of the listed plaquettes, a recount if the list overflowed,
+// and the copy to the host, all on the main stream, ending at ev_done.
+ah_status do_step2_diag(ah_sim *h, int64_t n)
+{
+    const View<float> vn = make_view(h->f32, h->cur, false);
+    DiagArgs da;
+    da.dc = diag_coef(h->cfg, n);
+    da.partials = h->partials;
+    da.list = h->list;
+    if (fused2_diag_ctas(h->N) > h->nparts)
+        return fail(AH_ERR_CUDA, "diagnostics scratch too small: the N=%d two-step pass needs %d partials, %d allocated",
+                    h->N, fused2_diag_ctas(h->N), h->nparts);
+    AH_CUDA(cudaMemsetAsync(h->list.count, 0, sizeof(unsigned long long), h->stream));
+    AH_CUDA(launch_fused2_diag(step2_view(h), h->N, kick_coef<float>(h->cfg, n), kick_coef<float>(h->cfg, n + 1), da,
+                               h->nparts, h->stream));
+    AH_CUDA(launch_diag_reduce<float>(vn, h->N, h->partials, fused2_diag_ctas(h->N), h->result, h->list,
+                                      h->diag_blocks, h->stream));
+    AH_CUDA(launch_wind_recount_on_overflow<float>(vn, h->N, h->list, h->result, h->diag_blocks, h->stream));
+    AH_CUDA(cudaMemcpyAsync(h->host_result, h->result, sizeof(DiagPartial), cudaMemcpyDeviceToHost, h->stream));
+    AH_CUDA(cudaEventRecord(h->ev_done, h->stream));
+    step2_swap(h);
     return AH_OK;
 }
 
@@ -386,6 +450,7 @@ ah_status do_diag(ah_sim *h, Box b, ah_obs *out)
         AH_CUDA(cudaStreamSynchronize(h->stream));
     }
     fill_obs(h->cfg, h->step, (int64_t)b.nx * b.ny * b.nz, *h->host_result, out);
+    if (whole) h->pierced_frac = (double)out->n_pierced / (3.0 * (double)h->nsites);
     if (out->nonfinite)
         return fail(AH_ERR_NONFINITE, "%lld sites have non-finite diagnostics", (long long)out->nonfinite);
     return AH_OK;
@@ -508,7 +573,7 @@ ah_status diag_start(ah_sim *h)
 
 extern "C" {
 
-int ah_abi_version(void) { return 4; }
+int ah_abi_version(void) { return 5; }
 
 const char *ah_last_error(void) { return g_err.c_str(); }
 
@@ -558,6 +623,7 @@ ah_status ah_create_ex(const ah_config *cfg, ah_sim **out)
     h->nsites = (long long)cfg->N * cfg->N * cfg->N;
     h->step = 0;
     h->cur = 0;
+    h->pierced_frac = 1.0;
     cudaError_t e = cudaGetDevice(&h->device);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking);
@@ -569,7 +635,7 @@ ah_status ah_create_ex(const ah_config *cfg, ah_sim **out)
     const size_t esz = cfg->precision == AH_FP32 ? sizeof(float) : sizeof(double);
     h->dbytes = (h->two_step ? 20 : 15) * padded((size_t)h->nsites) * esz;
     h->diag_blocks = diag_grid_blocks(h->num_sms);
-    const int nparts = std::max(h->diag_blocks, fused_diag_ctas(h->N));
+    const int nparts = std::max({ h->diag_blocks, fused_diag_ctas(h->N), h->two_step ? fused2_diag_ctas(h->N) : 0 });
     h->nparts = nparts;
     // expected near-cut plaquettes: about 5e-5 of the 3 N^3 plaquettes in FP32
     h->list.capacity = std::max<long long>(1LL << 20, h->nsites * 3 / 2000);
@@ -654,11 +720,18 @@ ah_status ah_step(ah_sim *h, int64_t nsteps)
     int64_t q = 0;
     if (h->two_step) {
         for (; q + 2 <= nsteps; q += 2) {
-            // the first pass after an asynchronous observables start reads the
-            // snapshot and writes the other set: it may overlap the pass
-            if (h->diag_pending && !h->diag_fenced && h->diag_free_pairs > 0) --h->diag_free_pairs;
-            else if ((st = diag_fence(h)) != AH_OK) return st;
-            if ((st = do_step2(h, h->step)) != AH_OK) return st;
+            if (h->diag_deferred) {
+                // the first pass after a deferred observables start takes it
+                h->diag_deferred = false;
+                if ((st = do_step2_diag(h, h->step)) != AH_OK) return st;
+                ++h->fused_diag_passes;
+            } else {
+                // the first pass after an asynchronous observables start reads
+                // the snapshot and writes the other set: it may overlap the pass
+                if (h->diag_pending && !h->diag_fenced && h->diag_free_pairs > 0) --h->diag_free_pairs;
+                else if ((st = diag_fence(h)) != AH_OK) return st;
+                if ((st = do_step2(h, h->step)) != AH_OK) return st;
+            }
             h->step += 2;
         }
     }
@@ -705,12 +778,26 @@ ah_status ah_observables_start(ah_sim *h)
         AH_CUDA(cudaEventCreateWithFlags(&h->ev_snap, cudaEventDisableTiming));
         AH_CUDA(cudaEventCreateWithFlags(&h->ev_done, cudaEventDisableTiming));
     }
+    h->diag_step = h->step;
+    // Fold the pass into the next two-step launch where that pays (measured at
+    // 256^3 - 1024^3: 2-4 % faster than a launch plus a separate pass on string
+    // networks in smooth fields, where most tiles skip the winding carries,
+    // 4-8 % slower on rough fields, where the fused launch's accumulators cost
+    // it a third of its resident CTAs)
+    const bool fuse = (h->cfg.flags & AH_FLAG_FUSED_DIAG) || h->pierced_frac < kFusedDiagPierced;
+    if (h->two_step && fuse && !(h->cfg.flags & AH_FLAG_EXACT_DIAG)) {
+        // taken by the next two-step launch (or run on its own before other work)
+        h->diag_pending = true;
+        h->diag_deferred = true;
+        h->diag_fenced = true;
+        h->diag_free_pairs = 0;
+        return AH_OK;
+    }
     st = h->cfg.precision == AH_FP32 ? diag_start<float>(h) : diag_start<double>(h);
     if (st != AH_OK) return st;
     h->diag_pending = true;
     h->diag_fenced = false;
     h->diag_free_pairs = h->two_step ? 1 : 0;
-    h->diag_step = h->step;
     return AH_OK;
 }
 
@@ -721,10 +808,12 @@ ah_status ah_observables_finish(ah_sim *h, ah_obs *out)
     if (st != AH_OK) return st;
     if (!out) return fail(AH_ERR_ARG, "null output");
     if (!h->diag_pending) return fail(AH_ERR_ARG, "no asynchronous observables pass was started");
+    if ((st = diag_undefer(h)) != AH_OK) return st;
     const cudaError_t e = cudaEventSynchronize(h->ev_done);
     h->diag_pending = false;
     if (e != cudaSuccess) return fail(AH_ERR_CUDA, "asynchronous observables: %s", cudaGetErrorString(e));
     fill_obs(h->cfg, h->diag_step, h->nsites, *h->host_result, out);
+    h->pierced_frac = (double)out->n_pierced / (3.0 * (double)h->nsites);
     if (out->nonfinite)
         return fail(AH_ERR_NONFINITE, "%lld sites have non-finite diagnostics", (long long)out->nonfinite);
     return AH_OK;
@@ -820,6 +909,7 @@ ah_status ah_get_info(const ah_sim *h, ah_info *out)
     out->n_variants = h->two_step ? fused2_variant_count() : n_variants(h->cfg.precision);
     const char *nm = variant_name(h, out->variant);
     snprintf(out->variant_name, sizeof out->variant_name, "%s", h->cfg.kernel == AH_KERNEL_PLAIN ? "plain" : nm);
+    out->fused_diag_passes = h->fused_diag_passes;
     return AH_OK;
 }
 

@@ -191,6 +191,21 @@ template <typename real>
 cudaError_t launch_diag_whole(const View<real> &v, int N, const DiagCoef &c, DiagPartial *partials,
                               int capacity, DiagPartial *result, DiagList list, int fix_blocks, cudaStream_t st);
 
+// Two leapfrog steps (as launch_fused2_step, tile 32 x 8) that also take the
+// whole-lattice diagnostics of the state n they read: one DiagPartial per CTA
+// (fused2_diag_ctas(N) of them; cudaErrorInvalidValue, nothing launched, if
+// that exceeds `capacity`), near-cut plaquettes appended to da.list, whose
+// count the caller clears first.  The state n stays in the buffers v reads.
+cudaError_t launch_fused2_diag(const View2<float> &v, int N, const KickCoef<float> &c1, const KickCoef<float> &c2,
+                               const DiagArgs &da, int capacity, cudaStream_t st);
+int fused2_diag_ctas(int N);
+// Sum n partials in a fixed order into *result, then add the FP64 windings of
+// the plaquettes listed in `list` (evaluated on the state v; fix_blocks x 128
+// threads).
+template <typename real>
+cudaError_t launch_diag_reduce(const View<real> &v, int N, const DiagPartial *partials, int n, DiagPartial *result,
+                               DiagList list, int fix_blocks, cudaStream_t st);
+
 // Host helpers of ah_api.cu shared with other translation units.
 KickCoef<float> host_kick_coef32(const ah_config &c, int64_t step);
 void host_carve32(Fields<float> &F, void *base, size_t nsites, bool spare = false);

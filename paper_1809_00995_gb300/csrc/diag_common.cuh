@@ -90,34 +90,47 @@ __device__ __forceinline__ int winding_carry(C2<T> z1, C2<T> z2, C2<T> z3, C2<T>
     return ok ? winding_scaled(z1, z2, z3, z4) : INT_MIN;
 }
 
+// 1 - cos Xi from e^{i Xi} = (c, s) without cancellation (in FP32 the
+// quotient by the fast approximate division, a few ulp)
+template <typename T>
+__device__ __forceinline__ T one_minus_cos(T c, T s)
+{
+    if constexpr (sizeof(T) == 4)
+        return c > 0.f ? __fdividef(s * s, 1.f + c) : 1.f - c;
+    else
+        return c > 0.0 ? s * s / (1.0 + c) : 1.0 - c;
+}
+
 // Double-float arithmetic (a value as the unevaluated sum hi + lo of two
 // floats) from error-free transformations: Knuth's TwoSum, Dekker's
-// Fast2Sum and the FMA-based TwoProduct.
+// Fast2Sum and the FMA-based TwoProduct.  The roundings are explicit
+// (__fadd_rn, __fmul_rn are never contracted into a multiply-add), so every
+// kernel that uses them gets the same bits from the same inputs.
 struct DF { float h, l; };
 __device__ __forceinline__ DF two_sum(float a, float b)
 {
-    const float s = a + b, bb = s - a;
-    return { s, (a - (s - bb)) + (b - bb) };
+    const float s = __fadd_rn(a, b), bb = __fsub_rn(s, a);
+    return { s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb)) };
 }
 __device__ __forceinline__ DF fast_two_sum(float a, float b)      // |a| >= |b| or a == 0
 {
-    const float s = a + b;
-    return { s, b - (s - a) };
+    const float s = __fadd_rn(a, b);
+    return { s, __fsub_rn(b, __fsub_rn(s, a)) };
 }
 __device__ __forceinline__ DF two_prod(float a, float b)
 {
-    const float p = a * b;
+    const float p = __fmul_rn(a, b);
     return { p, fmaf(a, b, -p) };
 }
 __device__ __forceinline__ DF df_add(DF a, DF b)
 {
     const DF s = two_sum(a.h, b.h);
-    return two_sum(s.h, s.l + (a.l + b.l));
+    return two_sum(s.h, __fadd_rn(s.l, __fadd_rn(a.l, b.l)));
 }
 __device__ __forceinline__ DF df_mul(DF a, DF b)
 {
     const DF p = two_prod(a.h, b.h);
-    return fast_two_sum(p.h, p.l + fmaf(a.h, b.l, a.l * b.h));
+    return fast_two_sum(p.h, __fadd_rn(p.l, fmaf(a.h, b.l, __fmul_rn(a.l, b.h))));
 }
 __host__ __device__ __forceinline__ DF df_from(double x)
 {
@@ -125,15 +138,16 @@ __host__ __device__ __forceinline__ DF df_from(double x)
     return { h, (float)(x - (double)h) };
 }
 
-// Compensated accumulator in the state precision (plain sum for FP64 data).
+// Compensated (Kahan) accumulator in the state precision (plain sum for FP64
+// data); explicit roundings, as for the double-float arithmetic.
 template <typename T>
 struct Acc {
     T s = 0, c = 0;
     __device__ __forceinline__ void add(T v)
     {
-        const T y = v - c;
-        const T t = s + y;
-        c = (t - s) - y;
+        const T y = __fsub_rn(v, c);
+        const T t = __fadd_rn(s, y);
+        c = __fsub_rn(__fsub_rn(t, s), y);
         s = t;
     }
     __device__ __forceinline__ double value() const { return (double)s - (double)c; }

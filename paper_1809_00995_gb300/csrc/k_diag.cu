@@ -416,10 +416,21 @@ cudaError_t launch_diag_whole(const View<real> &v, int N, const DiagCoef &c, Dia
     da.list = list;
     e = launch_fused_diag<real>(v, N, da, st);
     if (e != cudaSuccess) return e;
-    k_diag_sum<<<1, 1024, 0, st>>>(partials, fused_diag_ctas(N), result);
+    return launch_diag_reduce<real>(v, N, partials, fused_diag_ctas(N), result, list, fix_blocks, st);
+}
+
+template <typename real>
+cudaError_t launch_diag_reduce(const View<real> &v, int N, const DiagPartial *partials, int n, DiagPartial *result,
+                               DiagList list, int fix_blocks, cudaStream_t st)
+{
+    k_diag_sum<<<1, 1024, 0, st>>>(partials, n, result);
     k_diag_fixup<real><<<fix_blocks, 128, 0, st>>>(v, N, list, result);
     return cudaGetLastError();
 }
+template cudaError_t launch_diag_reduce<float>(const View<float> &, int, const DiagPartial *, int, DiagPartial *,
+                                               DiagList, int, cudaStream_t);
+template cudaError_t launch_diag_reduce<double>(const View<double> &, int, const DiagPartial *, int, DiagPartial *,
+                                                DiagList, int, cudaStream_t);
 template cudaError_t launch_diag_whole<float>(const View<float> &, int, const DiagCoef &, DiagPartial *, int,
                                               DiagPartial *, DiagList, int, cudaStream_t);
 template cudaError_t launch_diag_whole<double>(const View<double> &, int, const DiagCoef &, DiagPartial *, int,

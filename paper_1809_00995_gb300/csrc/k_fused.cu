@@ -39,17 +39,6 @@ namespace {
 // tile walk with nothing written back).
 enum { MODE_STEP = 0, MODE_DIAG = 1 };
 
-// 1 - cos Xi from e^{i Xi} = (c, s) without cancellation (in FP32 the
-// quotient by the fast approximate division, a few ulp)
-template <typename real>
-__device__ __forceinline__ real one_minus_cos(cpx<real> e)
-{
-    if constexpr (sizeof(real) == 4)
-        return e.r > 0.f ? __fdividef(e.i * e.i, 1.f + e.r) : 1.f - e.r;
-    else
-        return e.r > 0.0 ? e.i * e.i / (1.0 + e.r) : 1.0 - e.r;
-}
-
 // Each thread owns RX consecutive sites in x times RY rows (y stride 8).
 // One work item of the fused step: tile (bx, by) of plane chunk bz, marched in z.
 
@@ -290,7 +279,8 @@ __device__ __forceinline__ void fused_tile(const View<real> &v, int N, int zc, c
                 const cpx<real> x13 = plaq2(U0[e], U0[2 * NE + e + 1], U1p[e], U0[2 * NE + e]);
                 const cpx<real> x23 = plaq2(U0[NE + e], U0[2 * NE + e + EX], U1p[NE + e], U0[2 * NE + e]);
                 p12[m] = x12.i; p13[m] = x13.i; p23[m] = x23.i;
-                bcos[m] = one_minus_cos(x12) + one_minus_cos(x13) + one_minus_cos(x23);
+                bcos[m] = one_minus_cos(x12.r, x12.i) + one_minus_cos(x13.r, x13.i) +
+                          one_minus_cos(x23.r, x23.i);
             } else {
                 p12[m] = plaq(U0[e], U0[NE + e + 1], U0[e + EX], U0[NE + e]);
                 p13[m] = plaq(U0[e], U0[2 * NE + e + 1], U1p[e], U0[2 * NE + e]);

@@ -25,7 +25,15 @@
 // Each step evaluates the single-step kernel's formulas in the same order; the
 // results agree with single steps to FP32 rounding (the compiler is free to
 // fuse multiply-adds differently in the two kernels).
+//
+// k_fused2_diag is the same pass with the whole-lattice diagnostics of Sec. 2
+// (energy sums, Gauss residual, plaquette windings) of the state n folded into
+// the first step, which reads exactly that state: phi^n, theta^n and Pi, E at
+// n - 1/2, none of which the pass overwrites.  Each CTA accumulates them on the
+// sites it writes, so every site is counted once, and the diagnostics cost no
+// read of the state of their own.
 #include "ah_internal.cuh"
+#include "diag_common.cuh"
 #include "sincos32.cuh"
 #include "fused_common.cuh"
 
@@ -46,16 +54,142 @@ struct Geo2 {
     static constexpr size_t off_V = (off_P + sizeof(float) * 3 * NP + 15) / 16 * 16;
     static constexpr size_t off_Q = off_V + sizeof(cpx<float>) * 8 * NT;
     static constexpr size_t smem = off_Q + sizeof(float) * 3 * NT;
+    // k_fused2_diag: [2][NT] scaled edge products (d = 1, 3) and [NT] E_2 of
+    // plane q, read by the neighbouring row
+    static constexpr size_t off_D = (smem + 15) / 16 * 16;
+    static constexpr size_t smem_diag = off_D + sizeof(C2<float>) * 2 * NT + sizeof(float) * NT;
     static_assert(NHALO <= NT && NPHALO <= NT, "tile shape");
 };
 
 __device__ __forceinline__ cpx<float> cj(cpx<float> a) { return { a.r, -a.i }; }
+
+// Per-site diagnostic coefficients of step n in FP32 (the Gauss coefficients
+// as double-float pairs), converted on the host from DiagCoef.
+struct Diag2Coef {
+    float inv_dx2, v_coef, eel_coef, b_coef, sigma2;
+    DF g_div, g_phi;
+};
+struct Diag2Args {
+    Diag2Coef c;
+    DiagPartial *partials;     // one per CTA
+    DiagList list;             // plaquettes left to the FP64 path
+};
+
+// Scaled edge product conj(phi^a) U phi^b of a winding (Eq. 9).
+__device__ __forceinline__ C2<float> edge2(cpx<float> fa, cpx<float> u, cpx<float> fb)
+{
+    C2<float> z = cmul(conj(C2<float>{ fa.r, fa.i }), cmul(C2<float>{ u.r, u.i }, C2<float>{ fb.r, fb.i }));
+    unit_scale_or_nan(z);
+    return z;
+}
+
+// One thread's share of the whole-lattice diagnostics: the same per-site
+// terms, in the same order and precision, as the diagnostics pass of the
+// single-step tile walk (k_fused.cu, MODE_DIAG), so the two agree to FP32
+// rounding and the windings exactly.
+struct Diag2Acc {
+    // ah_obs.sums 3..13: K, |D phi|^2, V, E_el, B, K V, |D phi|^2 V, K L,
+    // |D phi|^2 L, p L, rho L (compensated; the sums of L, rho, p follow)
+    Acc<float> s[11];
+    Acc<float> g2, gs2;          // G^2 and scale^2 of the Gauss residual, times 2^60
+    DF gmax{ 0.f, 0.f };         // max |G|
+    float tmax = 0.f;            // max |theta|
+    int ic[kNumInt] = { 0, 0, 0, 0, 0, 0, 0, 0 };
+
+    // f0 = phi^x, w_d = U_d^x phi^{x+d}, E^{x - d}_d in e1b, e2b, e3b,
+    // bcos = sum over the three plaquettes at x of 1 - cos Xi
+    __device__ __forceinline__ void site(const Diag2Coef &c, float pr, float pim, cpx<float> f0, cpx<float> w1,
+                                         cpx<float> w2, cpx<float> w3, float e1, float e2, float e3, float e1b,
+                                         float e2b, float e3b, float bcos, float t1, float t2, float t3)
+    {
+        const float K = pr * pr + pim * pim;
+        const float d1r = w1.r - f0.r, d1i = w1.i - f0.i, d2r = w2.r - f0.r, d2i = w2.i - f0.i;
+        const float d3r = w3.r - f0.r, d3i = w3.i - f0.i;
+        const float G2 = (d1r * d1r + d1i * d1i + d2r * d2r + d2i * d2i + d3r * d3r + d3i * d3i) * c.inv_dx2;
+        const float m2 = f0.r * f0.r + f0.i * f0.i - c.sigma2;
+        const float V = c.v_coef * m2 * m2;
+        const float Eel = c.eel_coef * (e1 * e1 + e2 * e2 + e3 * e3);
+        const float B = c.b_coef * bcos;
+        const float L = K - G2 - V + Eel - B;
+        const float rho = K + G2 + V + Eel + B;
+        const float pp = K - G2 * (1.0f / 3.0f) - V + (Eel + B) * (1.0f / 3.0f);
+        s[0].add(K); s[1].add(G2);
+        s[2].add(V); s[3].add(Eel); s[4].add(B); s[5].add(K * V); s[6].add(G2 * V);
+        s[7].add(K * L); s[8].add(G2 * L); s[9].add(pp * L); s[10].add(rho * L);
+        tmax = fmaxf(tmax, fmaxf(fabsf(t1), fmaxf(fabsf(t2), fabsf(t3))));
+        ic[7] += !(isfinite(L) && isfinite(rho) && isfinite(pp));
+        // Gauss residual in double-float arithmetic
+        const DF div = df_add(df_add(two_sum(e1, -e1b), two_sum(e2, -e2b)), two_sum(e3, -e3b));
+        const DF a = two_prod(f0.r, pim), b = two_prod(f0.i, pr);
+        const DF g1 = df_mul(c.g_div, div), gq = df_mul(c.g_phi, df_add(a, { -b.h, -b.l }));
+        DF Gs = df_add(g1, gq);
+        if (Gs.h < 0.f) Gs = { -Gs.h, -Gs.l };
+        const float gs = fabsf(g1.h) + fabsf(gq.h);
+        const float sg = Gs.h * 0x1p30f, ss = gs * 0x1p30f;
+        g2.add(sg * sg);
+        gs2.add(ss * ss);
+        if (Gs.h > gmax.h || (Gs.h == gmax.h && Gs.l > gmax.l)) gmax = Gs;
+    }
+    // winding w of plaquette orientation q at site index `site`, or INT_MIN:
+    // the plaquette goes to the list for the FP64 path
+    __device__ __forceinline__ void wind(int q, int w, unsigned long long site, const DiagList &list)
+    {
+        if (w == INT_MIN) {
+            const unsigned long long k = atomicAdd(list.count, 1ULL);
+            if (k < (unsigned long long)list.capacity) list.items[k] = site * 4ULL + q;
+        } else {
+            ic[q] += w < 0 ? -w : w;
+            ic[3 + q] += w;
+            ic[6] += w != 0;
+        }
+    }
+    template <int NT>
+    __device__ __forceinline__ void flush(DiagPartial *out)
+    {
+        double accd[kNumSums];
+#pragma unroll
+        for (int k = 3; k < 14; ++k) accd[k] = s[k - 3].value();
+        accd[0] = accd[3] - accd[4] - accd[5] + accd[6] - accd[7];
+        accd[1] = accd[3] + accd[4] + accd[5] + accd[6] + accd[7];
+        accd[2] = accd[3] - accd[4] * (1.0 / 3.0) - accd[5] + (accd[6] + accd[7]) * (1.0 / 3.0);
+        accd[14] = g2.value() * 0x1p-60;
+        accd[15] = gs2.value() * 0x1p-60;
+        double mx[kNumMax] = { (double)gmax.h + (double)gmax.l, (double)tmax };
+        long long il[kNumInt];
+#pragma unroll
+        for (int k = 0; k < kNumInt; ++k) il[k] = ic[k];
+        block_reduce<NT>(accd, mx, il, out);
+    }
+};
 
 template <int TY, int MINB, typename IT>
 __global__ void __launch_bounds__(32 * TY, MINB)
     k_fused2(View2<float> v, int N, int zc, KickCoef<float> c1, KickCoef<float> c2)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    constexpr bool AH2_DIAG = false;
+    [[maybe_unused]] const Diag2Args da{};
+#define AH2_BX (int)blockIdx.x
+#define AH2_BY (int)blockIdx.y
+#define AH2_BZ (int)blockIdx.z
+#define AH2_SKIP_TILE return
+#include "k_fused2_tile.cuh"
+#undef AH2_BX
+#undef AH2_BY
+#undef AH2_BZ
+#undef AH2_SKIP_TILE
+}
+
+// The two-step pass with the diagnostics of the state n (tile 32 x 8, two
+// CTAs per SM: the accumulators take the register budget of a third); one
+// DiagPartial per CTA.
+template <typename IT>
+__global__ void __launch_bounds__(256, 2)
+    k_fused2_diag(View2<float> v, int N, int zc, KickCoef<float> c1, KickCoef<float> c2, Diag2Args da)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    constexpr int TY = 8;
+    constexpr bool AH2_DIAG = true;
 #define AH2_BX (int)blockIdx.x
 #define AH2_BY (int)blockIdx.y
 #define AH2_BZ (int)blockIdx.z
@@ -115,6 +249,8 @@ __global__ void __launch_bounds__(32 * TY, MINB)
         const int bz = local / (B.tiles2_x * B.tiles2_y);
         const int N = B.N, zc = B.zc2;
         using IT = int;
+        constexpr bool AH2_DIAG = false;
+        [[maybe_unused]] const Diag2Args da{};
 #define AH2_BX bx
 #define AH2_BY by
 #define AH2_BZ bz
@@ -236,6 +372,59 @@ cudaError_t launch_fused2_batch(int shape, const BatchLattice *lat, BatchState *
     case 1: return launch_batch2_shape<12, 2>(lat, state, nlat, items, nitems, counter, num_sms, st);
     default: return cudaErrorInvalidValue;
     }
+}
+
+// ---- two-step pass with the diagnostics of the state n ----
+void fused2_diag_grid(int N, int *tx, int *ty, int *nch, int *zc)
+{
+    using G = Geo2<8>;
+    *tx = (N + G::OX - 1) / G::OX;
+    *ty = (N + G::OY - 1) / G::OY;
+    const int n = choose_chunks(N, (long long)*tx * *ty, 2 * device_sm_count(), 16, 4);   // 2 CTAs / SM
+    *zc = (N + n - 1) / n;
+    *nch = (N + *zc - 1) / *zc;
+}
+
+int fused2_diag_ctas(int N)
+{
+    int tx, ty, nch, zc;
+    fused2_diag_grid(N, &tx, &ty, &nch, &zc);
+    return tx * ty * nch;
+}
+
+cudaError_t launch_fused2_diag(const View2<float> &v, int N, const KickCoef<float> &c1, const KickCoef<float> &c2,
+                               const DiagArgs &da, int capacity, cudaStream_t st)
+{
+    using G = Geo2<8>;
+    if (N < 4) return cudaErrorInvalidValue;
+    int tx, ty, nch, zc;
+    fused2_diag_grid(N, &tx, &ty, &nch, &zc);
+    if ((long long)tx * ty * nch > capacity) return cudaErrorInvalidValue;
+    static unsigned long long configured = 0;   // per device
+    const unsigned long long dev_bit = 1ULL << device_slot();
+    if (!(configured & dev_bit)) {
+        cudaError_t err = cudaFuncSetAttribute(k_fused2_diag<int>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)G::smem_diag);
+        if (err == cudaSuccess)
+            err = cudaFuncSetAttribute(k_fused2_diag<long long>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)G::smem_diag);
+        if (err != cudaSuccess) return err;
+        configured |= dev_bit;
+    }
+    Diag2Args a;
+    a.c.inv_dx2 = (float)da.dc.inv_dx2;
+    a.c.v_coef = (float)da.dc.v_coef;
+    a.c.eel_coef = (float)da.dc.eel_coef;
+    a.c.b_coef = (float)da.dc.b_coef;
+    a.c.sigma2 = (float)da.dc.sigma2;
+    a.c.g_div = df_from(da.dc.g_div);
+    a.c.g_phi = df_from(da.dc.g_phi);
+    a.partials = da.partials;
+    a.list = da.list;
+    const dim3 grid(tx, ty, nch);
+    if ((long long)N * N * N < (1LL << 31)) k_fused2_diag<int><<<grid, G::NT, G::smem_diag, st>>>(v, N, zc, c1, c2, a);
+    else k_fused2_diag<long long><<<grid, G::NT, G::smem_diag, st>>>(v, N, zc, c1, c2, a);
+    return cudaGetLastError();
 }
 
 int fused2_variant_count() { return (int)(sizeof(kShapes2) / sizeof(kShapes2[0])); }

@@ -4,7 +4,9 @@
 // (step n + 1).  It is included as the body of the single-lattice kernel and
 // inside the work-item loop of the batched kernel; in scope there: TY, IT, v
 // (View2<float>), N, zc, c1, c2, smem_raw (dynamic shared memory), and
-// AH2_SKIP_TILE, the statement that leaves an empty item.  (A function shared
+// AH2_SKIP_TILE, the statement that leaves an empty item, and AH2_DIAG (with
+// da, a Diag2Args), true in the kernel that also takes the diagnostics of the
+// state n on the written sites.  (A function shared
 // by the two kernels costs the single-lattice kernel a tenth of its speed:
 // its pointers and coefficients then no longer stay kernel parameters.)
 {
@@ -16,12 +18,21 @@
     float *sP = reinterpret_cast<float *>(smem_raw + G::off_P);
     C *sV = reinterpret_cast<C *>(smem_raw + G::off_V);      // [2][4][NT]
     float *sQ = reinterpret_cast<float *>(smem_raw + G::off_Q);
+    // AH2_DIAG: this thread's diagnostic sums; scaled edge products of R1
+    // (d = 1, 3) and E_2 of plane q for the row above / below
+    [[maybe_unused]] Diag2Acc dq;
+    [[maybe_unused]] C2<float> *sE = reinterpret_cast<C2<float> *>(smem_raw + G::off_D);    // [2][NT]
+    [[maybe_unused]] float *sG = reinterpret_cast<float *>(smem_raw + G::off_D + sizeof(C2<float>) * 2 * NT);
 
     const int tid = threadIdx.x, lx = tid & 31, wy = tid >> 5;
     // R1 origin; the written sites start one further in
     const int x0 = AH2_BX * G::OX - 1, y0 = AH2_BY * G::OY - 1;
     const int z0 = AH2_BZ * zc;
-    if (z0 >= N) AH2_SKIP_TILE;
+    if (z0 >= N) {
+        if constexpr (AH2_DIAG)
+            dq.flush<NT>(da.partials + (blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z)));
+        AH2_SKIP_TILE;
+    }
     const int z1 = min(z0 + zc, N);
     const IT NN = (IT)N * (IT)N;
 
@@ -83,6 +94,10 @@
     float q13_m = 0.f, q23_m = 0.f;
     // first-step results of the plane the second step works on
     float hpr = 0.f, hpi = 0.f, he1 = 0.f, he2 = 0.f, he3 = 0.f, ht1 = 0.f, ht2 = 0.f, ht3 = 0.f;
+    // AH2_DIAG: own scaled edges d = 1, 2 of plane q (computed one plane
+    // ahead) and E_3 of plane q - 1
+    [[maybe_unused]] C2<float> ed1{ 1.f, 0.f }, ed2{ 1.f, 0.f };
+    [[maybe_unused]] float e3_m = 0.f;
 
     // prologue: the first step starts at plane q0 = z0 - 1 (the second step
     // needs it below its first plane); ring slot of plane q: (q - q0 + 1) & 1
@@ -103,6 +118,9 @@
         p23_m = plaq(Um[NE + e], Um[2 * NE + e + EX], U0[NE + e], Um[2 * NE + e]);
     }
     __syncthreads();
+
+    // iterations k = 0 .. K - 1; the diagnostics cover planes q0 + 1 .. q0 + K - 2
+    const int K = z1 - z0 + 2;
 
     // iteration k: first step at plane q = q0 + k, second step at plane q - 1
     // (plaquettes from k = 1, kicks and stores from k = 2).  BC (compile
@@ -127,9 +145,19 @@
 
         // B: first-step plaquette sines of plane q on R1 and its low halos
         const C *U0 = sU + bc * 3 * NE, *U1p = sU + bn * 3 * NE;
-        const float p12 = plaq(U0[e], U0[NE + e + 1], U0[e + EX], U0[NE + e]);
-        const float p13 = plaq(U0[e], U0[2 * NE + e + 1], U1p[e], U0[2 * NE + e]);
-        const float p23 = plaq(U0[NE + e], U0[2 * NE + e + EX], U1p[NE + e], U0[2 * NE + e]);
+        float p12, p13, p23;
+        [[maybe_unused]] float bcos = 0.f;       // AH2_DIAG: sum of 1 - cos Xi at the own site
+        if constexpr (AH2_DIAG) {
+            const C x12 = plaq2(U0[e], U0[NE + e + 1], U0[e + EX], U0[NE + e]);
+            const C x13 = plaq2(U0[e], U0[2 * NE + e + 1], U1p[e], U0[2 * NE + e]);
+            const C x23 = plaq2(U0[NE + e], U0[2 * NE + e + EX], U1p[NE + e], U0[2 * NE + e]);
+            p12 = x12.i; p13 = x13.i; p23 = x23.i;
+            bcos = one_minus_cos(x12.r, x12.i) + one_minus_cos(x13.r, x13.i) + one_minus_cos(x23.r, x23.i);
+        } else {
+            p12 = plaq(U0[e], U0[NE + e + 1], U0[e + EX], U0[NE + e]);
+            p13 = plaq(U0[e], U0[2 * NE + e + 1], U1p[e], U0[2 * NE + e]);
+            p23 = plaq(U0[NE + e], U0[2 * NE + e + EX], U1p[NE + e], U0[2 * NE + e]);
+        }
         sP[p] = p12;
         sP[NP + p] = p13;
         sP[2 * NP + p] = p23;
@@ -140,7 +168,25 @@
             sP[NP + ph] = plaq(U0[eh], U0[2 * NE + eh + 1], U1p[eh], U0[2 * NE + eh]);
             sP[2 * NP + ph] = plaq(U0[NE + eh], U0[2 * NE + eh + EX], U1p[NE + eh], U0[2 * NE + eh]);
         }
-        __syncthreads();
+        // AH2_DIAG: the own edge d = 3 of plane q and d = 1, 2 of plane q + 1;
+        // a plaquette whose four edges all have |Arg| < pi/4 has W = 0, and
+        // when all edges of the CTA pass that test the carry chains are skipped
+        [[maybe_unused]] C2<float> ed3, ez1, ez2;
+        [[maybe_unused]] bool smooth_cta = false;
+        if constexpr (AH2_DIAG) {
+            const C *F1 = sF + bn * NE;
+            ed3 = edge2(ph_0, U0[2 * NE + e], ph_p);
+            ez1 = edge2(ph_p, U1p[e], F1[e + 1]);
+            ez2 = edge2(ph_p, U1p[NE + e], F1[e + EX]);
+            sE[r] = ed1;
+            sE[NT + r] = ed3;
+            sG[r] = e2;
+            auto smooth1 = [](const C2<float> &z) { return z.r > 1.001f * fabsf(z.i); };
+            const bool own_smooth = smooth1(ed1) && smooth1(ed2) && smooth1(ed3) && smooth1(ez1) && smooth1(ez2);
+            smooth_cta = __syncthreads_and(own_smooth) != 0;
+        } else {
+            __syncthreads();
+        }
 
         // C: first step (kicks and drifts) at the own site of plane q
         float npr, npi, ne1, ne2, ne3, nfr, nfi, nt[3];
@@ -167,6 +213,35 @@
             ne1 = c1.c_edamp * e1 + c1.c_cur * cu1 - c1.c_curl * cl1;
             ne2 = c1.c_edamp * e2 + c1.c_cur * cu2 - c1.c_curl * cl2;
             ne3 = c1.c_edamp * e3 + c1.c_cur * cu3 - c1.c_curl * cl3;
+            if constexpr (AH2_DIAG) {
+                // E_1 of x - 1 and the edges of x + 1 from the neighbouring
+                // lanes, E_2 of x - y and the edges of x + y from the rows
+                // below and above (every written site is inner to R1)
+                const float e1b = __shfl_up_sync(0xffffffffu, e1, 1);
+                const C2<float> z2_1 = { __shfl_down_sync(0xffffffffu, ed2.r, 1),
+                                         __shfl_down_sync(0xffffffffu, ed2.i, 1) };
+                const C2<float> z3_1 = { __shfl_down_sync(0xffffffffu, ed3.r, 1),
+                                         __shfl_down_sync(0xffffffffu, ed3.i, 1) };
+                if (wr && k >= 1 && k <= K - 2) {
+                    dq.site(da.c, pr, pim, f0, w1, w2, w3, e1, e2, e3, e1b, sG[r - TX], e3_m, bcos, th_0[0], th_0[1],
+                            th_0[2]);
+                    // windings of the plaquettes (12), (13), (23) based at x (Eq. 9)
+                    const C2<float> z1_2 = sE[r + TX], z3_2 = sE[NT + r + TX];
+                    int w12 = 0, w13 = 0, w23 = 0;
+                    if (!smooth_cta) {
+                        w12 = winding_scaled(ed1, z2_1, z1_2, ed2);
+                        w13 = winding_scaled(ed1, z3_1, ez1, ed3);
+                        w23 = winding_scaled(ed2, z3_2, ez2, ed3);
+                    }
+                    const unsigned long long site = (unsigned long long)q * (unsigned long long)NN + (unsigned)roff;
+                    dq.wind(0, w12, site, da.list);
+                    dq.wind(1, w13, site, da.list);
+                    dq.wind(2, w23, site, da.list);
+                }
+                e3_m = e3;
+                ed1 = ez1;
+                ed2 = ez2;
+            }
             nfr = f0.r + c1.dt * npr;
             nfi = f0.i + c1.dt * npi;
             nt[0] = th_0[0] + c1.dt * ne1;
@@ -257,9 +332,10 @@
         hpr = npr; hpi = npi; he1 = ne1; he2 = ne2; he3 = ne3;
         ht1 = nt[0]; ht2 = nt[1]; ht3 = nt[2];
     };
-    const int K = z1 - z0 + 2;
     for (int k = 0; k < K; k += 2) {
         iter(k, IC<1>{});
         if (k + 1 < K) iter(k + 1, IC<0>{});
     }
+    if constexpr (AH2_DIAG)
+        dq.flush<NT>(da.partials + (blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z)));
 }

@@ -3,7 +3,9 @@
 The pass reads the state at the start (the snapshot) on a second stream while
 later steps go on; a launch that would overwrite the snapshot waits for it.  The
 result must be that of ah_observables on the same state, and the evolution must
-be exactly the one without the pass."""
+be exactly the one without the pass.  (A two-step simulation may hand the pass
+to its next two-step launch instead; it does so here only when asked to, or on
+states with few pierced plaquettes: test_gpu_fused_diag.py.)"""
 import numpy as np
 import pytest
 

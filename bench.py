@@ -452,6 +452,7 @@ def main():
     start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     barrier()
     torch.cuda.synchronize()
+    weak0 = g.info["weak_field_launches"]
     start.record(stream)
     for k in range(a.steps):
         obs = bench_step(*ev[k])
@@ -465,6 +466,7 @@ def main():
     value = job_value(world, n_sites, diag_every * a.steps, t_max / 1e3)
 
     variant_name = info["variant_name"]
+    weak_launches = g.info["weak_field_launches"] - weak0
     g.close()
 
     # end to end through the public C ABI, host clock: one whole job as a user
@@ -511,7 +513,9 @@ def main():
                 "ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch at %d^3 (%.2f B/site), "
                 "scaled to %d^3 by the site count" % (trec["N"], trec["dram_bytes_per_site"], N),
                 "kernel": ("fused step, shape %s (one leapfrog step per launch)" % variant_name if not two_step else
-                           "two-step fused kernel, shape %s (two leapfrog steps per launch)" % variant_name),
+                           "two-step fused kernel, shape %s (two leapfrog steps per launch; %d of the %d timed "
+                           "launches the form for weak gauge fields)"
+                           % (variant_name, weak_launches, a.steps * diag_every // steps_per_launch)),
                 "peak_source": peak_src,
                 "alg_bytes_per_launch": alg_bytes, "avg_launch_ms": avg_launch_s * 1e3,
                 "step_share_of_time": step_ms / t_ms}

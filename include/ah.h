@@ -96,6 +96,11 @@ enum { AH_FLAG_EXACT_DIAG = 1, AH_FLAG_AUTOTUNE = 2, AH_FLAG_WRAP_THETA = 4, AH_
  * variant_name refer to the two-step shapes, and the TMA-fed single-step
  * shapes are not available.  Refused (AH_ERR_ARG) for FP64 and for
  * AH_KERNEL_PLAIN.
+ * In this mode, while the last whole-lattice observables of the simulation
+ * found max |theta| <= 2^-7 (weak gauge fields: early times, small scale
+ * factors), the pairs run a kernel whose link exponentials take two-term
+ * sine/cosine forms in warps whose phases are all within 2^-6 (within an ulp
+ * of the general forms; ah_info.weak_field_launches counts those launches).
  * FUSED_DIAG (with TWO_STEP only, else AH_ERR_ARG): an asynchronous
  * observables pass (ah_observables_start) is always taken by the next
  * two-step launch, which reads the state of the pass for its first step
@@ -262,6 +267,10 @@ typedef struct ah_info {
     char variant_name[32];
     int64_t fused_diag_passes;   /* observables passes taken by two-step
                                     launches so far (AH_FLAG_FUSED_DIAG)   */
+    int64_t weak_field_launches; /* two-step launches so far that used the
+                                    kernel for weak gauge fields (taken
+                                    while the last whole-lattice observables
+                                    found max |theta| <= 2^-7)             */
 } ah_info;
 ah_status ah_get_info(const ah_sim *sim, ah_info *out);
 

@@ -91,7 +91,8 @@ class ah_info(ctypes.Structure):
     _fields_ = [("N", ctypes.c_int64), ("n_sites", ctypes.c_int64), ("precision", ctypes.c_int32),
                 ("kernel", ctypes.c_int32), ("state_bytes", ctypes.c_int64), ("step_bytes", ctypes.c_int64),
                 ("step_launches", ctypes.c_int64), ("variant", ctypes.c_int32), ("n_variants", ctypes.c_int32),
-                ("variant_name", ctypes.c_char * 32), ("fused_diag_passes", ctypes.c_int64)]
+                ("variant_name", ctypes.c_char * 32), ("fused_diag_passes", ctypes.c_int64),
+                ("weak_field_launches", ctypes.c_int64)]
 
 
 _SIGS = {

@@ -158,6 +158,10 @@ struct ah_sim {
     // fraction of the plaquettes pierced at the last whole-lattice observables
     // (1 before any): picks the fused or the separate pass for a deferral
     double pierced_frac;
+    // the last whole-lattice observables found max |theta| <= kWeakTheta: the
+    // two-step launches use the kernel specialised to weak gauge fields
+    bool weak_links;
+    int64_t weak_launches;
     int diag_free_pairs;
     int64_t diag_step;
 };
@@ -167,6 +171,11 @@ namespace {
 // Largest fraction of pierced plaquettes at which a deferred observables pass
 // rides on the next two-step launch (k_fused2_diag) without AH_FLAG_FUSED_DIAG.
 constexpr double kFusedDiagPierced = 1e-3;
+// Largest max |theta| at the last whole-lattice observables for which the
+// two-step launches take the kernel specialised to weak gauge fields (half the
+// bound of its short sine/cosine forms, 2^-6, so the phases may double before
+// the next observables; beyond it the kernel stays correct, only slower).
+constexpr double kWeakTheta = 0x1p-7;
 
 template <typename real>
 void carve(Fields<real> &F, char *base, size_t n, bool spare = false)
@@ -370,10 +379,18 @@ void step2_swap(ah_sim *h)
 }
 ah_status do_step2(ah_sim *h, int64_t n)
 {
+    const bool weak = h->weak_links && fused2_weak_ok(h->variant2, h->N);
     AH_CUDA(launch_fused2_step(step2_view(h), h->N, kick_coef<float>(h->cfg, n), kick_coef<float>(h->cfg, n + 1),
-                               h->variant2, h->stream));
+                               h->variant2, h->stream, weak));
+    h->weak_launches += weak;
     step2_swap(h);
     return AH_OK;
+}
+// What the last whole-lattice observables say about the state.
+void note_obs(ah_sim *h, const ah_obs &o)
+{
+    h->pierced_frac = (double)o.n_pierced / (3.0 * (double)h->nsites);
+    h->weak_links = h->two_step && o.max_abs_theta <= kWeakTheta;
 }
 // The same pass taking the deferred observables of the state n on the way:
 // partial sums, then (on the state n, which the pass leaves in place) the
@@ -450,7 +467,7 @@ ah_status do_diag(ah_sim *h, Box b, ah_obs *out)
         AH_CUDA(cudaStreamSynchronize(h->stream));
     }
     fill_obs(h->cfg, h->step, (int64_t)b.nx * b.ny * b.nz, *h->host_result, out);
-    if (whole) h->pierced_frac = (double)out->n_pierced / (3.0 * (double)h->nsites);
+    if (whole) note_obs(h, *out);
     if (out->nonfinite)
         return fail(AH_ERR_NONFINITE, "%lld sites have non-finite diagnostics", (long long)out->nonfinite);
     return AH_OK;
@@ -813,7 +830,7 @@ ah_status ah_observables_finish(ah_sim *h, ah_obs *out)
     h->diag_pending = false;
     if (e != cudaSuccess) return fail(AH_ERR_CUDA, "asynchronous observables: %s", cudaGetErrorString(e));
     fill_obs(h->cfg, h->diag_step, h->nsites, *h->host_result, out);
-    h->pierced_frac = (double)out->n_pierced / (3.0 * (double)h->nsites);
+    note_obs(h, *out);
     if (out->nonfinite)
         return fail(AH_ERR_NONFINITE, "%lld sites have non-finite diagnostics", (long long)out->nonfinite);
     return AH_OK;
@@ -861,6 +878,8 @@ ah_status ah_set_fields(ah_sim *h, const double *in, int64_t step)
     if (e != cudaSuccess) return fail(AH_ERR_CUDA, "set_fields failed: %s", cudaGetErrorString(e));
     h->step = step;
     h->pristine = false;
+    h->pierced_frac = 1.0;              // nothing known about the new state
+    h->weak_links = false;
     return AH_OK;
 }
 
@@ -910,6 +929,7 @@ ah_status ah_get_info(const ah_sim *h, ah_info *out)
     const char *nm = variant_name(h, out->variant);
     snprintf(out->variant_name, sizeof out->variant_name, "%s", h->cfg.kernel == AH_KERNEL_PLAIN ? "plain" : nm);
     out->fused_diag_passes = h->fused_diag_passes;
+    out->weak_field_launches = h->weak_launches;
     return AH_OK;
 }
 

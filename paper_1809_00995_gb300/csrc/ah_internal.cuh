@@ -150,8 +150,12 @@ int fused_default_variant();
 
 // Two leapfrog steps (coefficients c1 for step n, c2 for step n + 1) in one
 // pass, FP32; shape `variant` in [0, fused2_variant_count()).
+// weak: the kernel specialised to weak gauge fields (link phases mostly in
+// [-2^-6, 2^-6]; same update, within an ulp per link exponential), available
+// where fused2_weak_ok(variant, N).
 cudaError_t launch_fused2_step(const View2<float> &v, int N, const KickCoef<float> &c1, const KickCoef<float> &c2,
-                               int variant, cudaStream_t st);
+                               int variant, cudaStream_t st, bool weak = false);
+bool fused2_weak_ok(int variant, int N);
 int fused2_variant_count();
 const char *fused2_variant_name(int variant);
 int fused2_default_variant();

@@ -162,12 +162,15 @@ struct Diag2Acc {
     }
 };
 
-template <int TY, int MINB, typename IT>
+// WEAK: the link exponentials by sincos_link3_weak (a kernel for states whose
+// link phases are mostly within [-2^-6, 2^-6]; correct for any state).
+template <int TY, int MINB, typename IT, bool WEAK = false>
 __global__ void __launch_bounds__(32 * TY, MINB)
     k_fused2(View2<float> v, int N, int zc, KickCoef<float> c1, KickCoef<float> c2)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     constexpr bool AH2_DIAG = false;
+    constexpr bool AH2_WEAK = WEAK;
     [[maybe_unused]] const Diag2Args da{};
 #define AH2_BX (int)blockIdx.x
 #define AH2_BY (int)blockIdx.y
@@ -190,6 +193,7 @@ __global__ void __launch_bounds__(256, 2)
     extern __shared__ __align__(16) unsigned char smem_raw[];
     constexpr int TY = 8;
     constexpr bool AH2_DIAG = true;
+    constexpr bool AH2_WEAK = false;
 #define AH2_BX (int)blockIdx.x
 #define AH2_BY (int)blockIdx.y
 #define AH2_BZ (int)blockIdx.z
@@ -250,6 +254,7 @@ __global__ void __launch_bounds__(32 * TY, MINB)
         const int N = B.N, zc = B.zc2;
         using IT = int;
         constexpr bool AH2_DIAG = false;
+        constexpr bool AH2_WEAK = false;
         [[maybe_unused]] const Diag2Args da{};
 #define AH2_BX bx
 #define AH2_BY by
@@ -286,7 +291,8 @@ struct Shape2 { int ty, minb; const char *name; };
 constexpr Shape2 kShapes2[] = { { 8, 2, "two_ty8_b2" }, { 8, 3, "two_ty8_b3" }, { 16, 1, "two_ty16_b1" },
                                 { 12, 2, "two_ty12_b2" } };
 
-template <int TY, int MINB>
+// WEAK (32-bit site indices only; the caller checks fused2_weak_ok)
+template <int TY, int MINB, bool WEAK = false>
 cudaError_t launch_shape2(const View2<float> &v, int N, const KickCoef<float> &c1, const KickCoef<float> &c2,
                           cudaStream_t st)
 {
@@ -295,9 +301,9 @@ cudaError_t launch_shape2(const View2<float> &v, int N, const KickCoef<float> &c
     static unsigned long long configured = 0;   // per device, once per instantiation
     const unsigned long long dev_bit = 1ULL << device_slot();
     if (!(configured & dev_bit)) {
-        cudaError_t err = cudaFuncSetAttribute(k_fused2<TY, MINB, int>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                               (int)G::smem);
-        if (err == cudaSuccess)
+        cudaError_t err = cudaFuncSetAttribute(k_fused2<TY, MINB, int, WEAK>,
+                                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::smem);
+        if (err == cudaSuccess && !WEAK)
             err = cudaFuncSetAttribute(k_fused2<TY, MINB, long long>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)G::smem);
         if (err != cudaSuccess) return err;
@@ -308,17 +314,26 @@ cudaError_t launch_shape2(const View2<float> &v, int N, const KickCoef<float> &c
     int nch = choose_chunks(N, (long long)tx * ty, device_sm_count() * MINB, 16, 4);
     const int zc = (N + nch - 1) / nch;
     nch = (N + zc - 1) / zc;
-    if (idx32) k_fused2<TY, MINB, int><<<dim3(tx, ty, nch), G::NT, G::smem, st>>>(v, N, zc, c1, c2);
-    else k_fused2<TY, MINB, long long><<<dim3(tx, ty, nch), G::NT, G::smem, st>>>(v, N, zc, c1, c2);
+    if constexpr (WEAK) {
+        if (!idx32) return cudaErrorInvalidValue;
+        k_fused2<TY, MINB, int, true><<<dim3(tx, ty, nch), G::NT, G::smem, st>>>(v, N, zc, c1, c2);
+    } else if (idx32) {
+        k_fused2<TY, MINB, int><<<dim3(tx, ty, nch), G::NT, G::smem, st>>>(v, N, zc, c1, c2);
+    } else {
+        k_fused2<TY, MINB, long long><<<dim3(tx, ty, nch), G::NT, G::smem, st>>>(v, N, zc, c1, c2);
+    }
     return cudaGetLastError();
 }
 
 }  // namespace
 
+bool fused2_weak_ok(int variant, int N) { return variant == 1 && (long long)N * N * N < (1LL << 31); }
+
 cudaError_t launch_fused2_step(const View2<float> &v, int N, const KickCoef<float> &c1, const KickCoef<float> &c2,
-                               int variant, cudaStream_t st)
+                               int variant, cudaStream_t st, bool weak)
 {
     if (N < 4) return cudaErrorInvalidValue;
+    if (weak) return fused2_weak_ok(variant, N) ? launch_shape2<8, 3, true>(v, N, c1, c2, st) : cudaErrorInvalidValue;
     switch (variant) {
     case 0: return launch_shape2<8, 2>(v, N, c1, c2, st);
     case 1: return launch_shape2<8, 3>(v, N, c1, c2, st);

@@ -4,9 +4,10 @@
 // (step n + 1).  It is included as the body of the single-lattice kernel and
 // inside the work-item loop of the batched kernel; in scope there: TY, IT, v
 // (View2<float>), N, zc, c1, c2, smem_raw (dynamic shared memory), and
-// AH2_SKIP_TILE, the statement that leaves an empty item, and AH2_DIAG (with
-// da, a Diag2Args), true in the kernel that also takes the diagnostics of the
-// state n on the written sites.  (A function shared
+// AH2_SKIP_TILE, the statement that leaves an empty item, AH2_DIAG (with da,
+// a Diag2Args), true in the kernel that also takes the diagnostics of the
+// state n on the written sites, and AH2_WEAK, true in the kernel specialised
+// to weak gauge fields (sincos_link3_weak).  (A function shared
 // by the two kernels costs the single-lattice kernel a tenth of its speed:
 // its pointers and coefficients then no longer stay kernel parameters.)
 {
@@ -78,7 +79,8 @@
             if (t == 0 || has_halo) {
                 const int ei = t == 0 ? e : heix;
                 float sn[3], co[3];
-                sincos_link3(fth[t], sn, co);
+                if constexpr (AH2_WEAK) sincos_link3_weak(fth[t], sn, co);
+                else sincos_link3(fth[t], sn, co);
 #pragma unroll
                 for (int d = 0; d < 3; ++d) sU[(b * 3 + d) * NE + ei] = { co[d], sn[d] };
                 sF[b * NE + ei] = { fph[t][0], fph[t][1] };
@@ -261,7 +263,8 @@
         th_0[0] = tp0; th_0[1] = tp1; th_0[2] = tp2;
         // U' = e^{i theta'} and phi' of plane q into the second step's ring
         float sn[3], co[3];
-        sincos_link3(nt, sn, co);
+        if constexpr (AH2_WEAK) sincos_link3_weak(nt, sn, co);
+        else sincos_link3(nt, sn, co);
         C *Vq = sV + (1 - bc) * 4 * NT;
         Vq[r] = { co[0], sn[0] };
         Vq[NT + r] = { co[1], sn[1] };

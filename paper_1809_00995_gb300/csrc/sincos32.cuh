@@ -65,6 +65,37 @@ __device__ __forceinline__ void sincos_link3(const float t[3], float s[3], float
     }
 }
 
+// sin r, cos r on |r| <= 2^-6 by the first two Taylor terms of each, r - r^3/3!
+// and 1 - r^2/2!: the next terms are below |r| r^4/5! <= 2^-24 |r| / 120 and
+// r^4/4! <= 2^-24 / 24, a few hundredths of an ulp of the results, so both
+// stay within an ulp of the longer polynomials (and of sin, cos).
+__device__ __forceinline__ void sincos_small(float r, float *s, float *c)
+{
+    const float r2 = r * r;
+    *s = fmaf(r * r2, -1.666666716e-01f, r);
+    *c = fmaf(r2, -0.5f, 1.0f);
+}
+
+// sincos_link3 for kernels specialised to weak gauge fields: one warp
+// reduction of the largest |phase| picks the two-term forms when every phase
+// of the active lanes is in [-2^-6, 2^-6], else the choice of sincos_link3.
+// (In kernels for general states the extra tier costs more than it saves.)
+__device__ __forceinline__ void sincos_link3_weak(const float t[3], float s[3], float c[3])
+{
+    const float m = fmaxf(fabsf(t[0]), fmaxf(fabsf(t[1]), fabsf(t[2])));
+    const unsigned mb = __reduce_max_sync(__activemask(), __float_as_uint(m));   // m >= 0: bits order as values
+    if (mb <= __float_as_uint(0x1p-6f)) {
+#pragma unroll
+        for (int d = 0; d < 3; ++d) sincos_small(t[d], &s[d], &c[d]);
+    } else if (mb <= __float_as_uint(0.78f)) {
+#pragma unroll
+        for (int d = 0; d < 3; ++d) sincos_poly(t[d], &s[d], &c[d]);
+    } else {
+#pragma unroll
+        for (int d = 0; d < 3; ++d) sincos_link(t[d], &s[d], &c[d]);
+    }
+}
+
 __device__ __forceinline__ void sincos_link(double t, double *s, double *c) { sincos(t, s, c); }
 __device__ __forceinline__ void sincos_link3(const double t[3], double s[3], double c[3])
 {

@@ -36,11 +36,11 @@ def test_abi_version_and_struct_layouts(tmp_path):
     assert ah.ah_abi_version() == 5
     src = tmp_path / "sz.c"
     src.write_text('#include "ah.h"\n#include <stdio.h>\n#include <stddef.h>\n'
-                   'int main(void){printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\\n", sizeof(ah_config), sizeof(ah_obs),'
+                   'int main(void){printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\\n", sizeof(ah_config), sizeof(ah_obs),'
                    ' sizeof(ah_info), offsetof(ah_obs, sums), offsetof(ah_obs, nonfinite),'
                    ' offsetof(ah_config, seed), offsetof(ah_info, variant_name), sizeof(ah_sums), sizeof(ah_batch_stats),'
                    ' sizeof(ah_server_stats), sizeof(ah_window), offsetof(ah_window, out),'
-                   ' offsetof(ah_info, fused_diag_passes));return 0;}\n')
+                   ' offsetof(ah_info, fused_diag_passes), offsetof(ah_info, weak_field_launches));return 0;}\n')
     exe = tmp_path / "sz"
     subprocess.run(["gcc", "-I" + os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
     got = [int(v) for v in subprocess.run([str(exe)], capture_output=True, text=True).stdout.split()]
@@ -48,7 +48,7 @@ def test_abi_version_and_struct_layouts(tmp_path):
             ah.ah_obs.sums.offset, ah.ah_obs.nonfinite.offset, ah.ah_config.seed.offset,
             ah.ah_info.variant_name.offset, ctypes.sizeof(ah.ah_sums), ctypes.sizeof(ah.ah_batch_stats),
             ctypes.sizeof(ah.ah_server_stats), ctypes.sizeof(ah.ah_window), ah.ah_window.out.offset,
-            ah.ah_info.fused_diag_passes.offset]
+            ah.ah_info.fused_diag_passes.offset, ah.ah_info.weak_field_launches.offset]
     assert got == want
 
 

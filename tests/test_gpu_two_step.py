@@ -156,3 +156,45 @@ def test_1300cubed_two_step_64bit_site_indices():
             O.evolve(p, win32, 0, k)
             got = g.fields(*org, b, b, b)
             assert max(rel_err(got, win32[:, k:k + b, k:k + b, k:k + b])) <= TOL32, org
+
+
+@pytest.mark.parametrize("th_amp,e_amp", [(2e-4, 1e-4), (7e-3, 0.3)])
+def test_weak_field_kernel_matches_oracle(th_amp, e_amp):
+    """After whole-lattice observables with max |theta| <= 2^-7 the pairs run
+    the kernel specialised to weak gauge fields: (a) phases that stay tiny, so
+    every warp takes the two-term sine/cosine forms; (b) phases just below
+    2^-7 that the electric field drives past 2^-6 within a step, so warps fall
+    back to the polynomials.  Both equal the oracle and the general two-step
+    kernel after 20 steps."""
+    N = 40
+    f = random_state(N, 61, th_amp=th_amp, e_amp=e_amp)
+    p = O.Params(N=N, era=ah.AH_MATTER, s=1.0, seed=1, tau_ref=9.0)
+    with ah.Sim(N, era=ah.AH_MATTER, s=1.0, seed=1, flags=TWO, tau_ref=9.0) as g:
+        g.set_fields(f, step=3)
+        f0 = g.fields()
+        assert g.observables()["max_abs_theta"] <= 2.0 ** -7
+        g.step(20)
+        got = g.fields()
+        assert g.info["weak_field_launches"] == 10
+    _, general, _ = run(N, f, 20, TWO, ah.AH_MATTER, 1.0, tau_ref=9.0)   # no observables first: general kernel
+    ref = O.evolve(p, f0.copy(), 3, 20)
+    assert max(rel_err(got, ref)) <= TOL32, rel_err(got, ref)
+    assert max(rel_err(got, general)) <= TOL32, rel_err(got, general)
+
+
+def test_strong_fields_and_new_fields_keep_the_general_kernel():
+    """Phases beyond 2^-7 at the last observables, or fields set since, keep
+    the general two-step kernel."""
+    N = 24
+    with ah.Sim(N, flags=TWO) as g:
+        g.set_fields(random_state(N, 62, th_amp=0.4), 0)
+        g.observables()
+        g.step(4)
+        assert g.info["weak_field_launches"] == 0
+        g.set_fields(random_state(N, 63, th_amp=1e-4), 4)
+        assert g.observables()["max_abs_theta"] <= 2.0 ** -7
+        g.step(2)
+        assert g.info["weak_field_launches"] == 1
+        g.set_fields(random_state(N, 63, th_amp=1e-4), 6)
+        g.step(2)
+        assert g.info["weak_field_launches"] == 1

@@ -140,6 +140,29 @@ def test_1024cubed_two_step_light_cone_windows():
     assert o["n_sites"] == N ** 3 and o["nonfinite"] == 0 and o["gauss_rel"] < 1e-5
 
 
+def test_1024cubed_weak_field_kernel_light_cone_windows():
+    """The launches the bench times: the 1024^3 bench lattice in two-step mode
+    after whole-lattice observables at step 0 (max |theta| = 0), so all ten
+    passes of 20 steps run the kernel for weak gauge fields; three 16^3
+    windows, two across the periodic seam, equal the oracle's evolution of
+    (16 + 2*20)^3 windows."""
+    N, k, b = 1024, 20, 16
+    p = O.Params(N=N, era=ah.AH_MATTER, s=1.0, seed=3)
+    with ah.Sim(N, era=ah.AH_MATTER, s=1.0, seed=3, flags=TWO) as g:
+        assert g.observables()["max_abs_theta"] <= 2.0 ** -7
+        g.step(k)
+        assert g.info["weak_field_launches"] == k // 2
+        for org in [(1020, 1013, 2), (77, 1015, 1009), (640, 333, 511)]:
+            M = b + 2 * k
+            win = O.init(p, M=M, origin=[(o - k) % N for o in org])
+            win32 = win.astype(np.float32).astype(np.float64)
+            O.evolve(p, win32, 0, k)
+            got = g.fields(*org, b, b, b)
+            assert max(rel_err(got, win32[:, k:k + b, k:k + b, k:k + b])) <= TOL32, org
+        o = g.observables()
+    assert o["nonfinite"] == 0 and o["gauss_rel"] < 1e-5
+
+
 def test_1300cubed_two_step_64bit_site_indices():
     """N^3 >= 2^31 takes the 64-bit-index instantiation: 1300^3 FP32 in two-step
     mode (20 arrays, 176 GB); windows beyond linear index 2^31 and across the

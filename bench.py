@@ -304,6 +304,7 @@ def run_batch1024(ah, peak, flags=0, N=1024, short=40, long=100):
             "ms_per_step": ms, "site_updates_per_s": N ** 3 / (ms / 1e3), "alg_gbs": gbs, "peak_gbs": peak,
             "hbm_frac": gbs / peak, "effective": bool(flags & ah.AH_BATCH_TWO_STEP),
             "launches_per_step": (b["launches"] - a["launches"]) / (long - short),
+            "weak_field_launches": b.get("weak_field_launches", 0),
             "method": "difference of %d- and %d-step batch jobs (wall clock), 80 B per site-update" % (long, short)}
 
 

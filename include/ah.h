@@ -321,6 +321,10 @@ typedef struct ah_batch_stats {
                                 shape with AH_BATCH_TWO_STEP)                    */
     int32_t rounds;          /* graph (or launch-sequence) replays               */
     int64_t launches;        /* kernel launches of the batched steps             */
+    int64_t weak_field_launches; /* two-step launches of paired lattices of side
+                                >= 512 in the form for weak gauge fields (taken
+                                while the lattice's last observables found
+                                max |theta| <= 2^-7, as for ah_step)             */
 } ah_batch_stats;
 
 /* Run `count` lattices (cfgs[i]: precision AH_FP32, N <= 1290; each runs

@@ -72,7 +72,7 @@ class ah_obs(ctypes.Structure):
 class ah_batch_stats(ctypes.Structure):
     _fields_ = [("seconds", ctypes.c_double), ("setup_seconds", ctypes.c_double), ("site_updates", ctypes.c_double),
                 ("sims_per_hour", ctypes.c_double), ("shape", ctypes.c_int32), ("rounds", ctypes.c_int32),
-                ("launches", ctypes.c_int64)]
+                ("launches", ctypes.c_int64), ("weak_field_launches", ctypes.c_int64)]
 
 
 class ah_window(ctypes.Structure):

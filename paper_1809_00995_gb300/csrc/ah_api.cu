@@ -171,11 +171,6 @@ namespace {
 // Largest fraction of pierced plaquettes at which a deferred observables pass
 // rides on the next two-step launch (k_fused2_diag) without AH_FLAG_FUSED_DIAG.
 constexpr double kFusedDiagPierced = 1e-3;
-// Largest max |theta| at the last whole-lattice observables for which the
-// two-step launches take the kernel specialised to weak gauge fields (half the
-// bound of its short sine/cosine forms, 2^-6, so the phases may double before
-// the next observables; beyond it the kernel stays correct, only slower).
-constexpr double kWeakTheta = 0x1p-7;
 
 template <typename real>
 void carve(Fields<real> &F, char *base, size_t n, bool spare = false)
@@ -590,7 +585,7 @@ ah_status diag_start(ah_sim *h)
 
 extern "C" {
 
-int ah_abi_version(void) { return 5; }
+int ah_abi_version(void) { return 6; }
 
 const char *ah_last_error(void) { return g_err.c_str(); }
 

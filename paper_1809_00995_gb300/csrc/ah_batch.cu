@@ -72,6 +72,7 @@ struct Lat {
     long long nsites = 0;
     int nsteps = 0, step = 0, cur = 0, pe = 0;
     bool two = false;                 // stepped in pairs (second Pi/E set for the two-step pass)
+    bool weak = false;                // its last observables found max |theta| <= kWeakTheta (paired lattices)
     void *mem = nullptr;
     size_t bytes = 0;
     Fields<float> F{};
@@ -189,6 +190,7 @@ struct Engine {
     std::map<std::tuple<int, int, int>, cudaGraphExec_t> graphs;
     bool use_graph = true;
     long long launches = 0;
+    long long weak_launches = 0;   // direct two-step launches in the form for weak gauge fields
     int rounds = 0;
 
     cudaError_t init(bool graph, bool two_step)
@@ -341,8 +343,11 @@ struct Engine {
         v.oth1 = F.th[o][0]; v.oth2 = F.th[o][1]; v.oth3 = F.th[o][2];
         v.opir = oq[0]; v.opii = oq[1]; v.oe1 = oq[2]; v.oe2 = oq[3]; v.oe3 = oq[4];
         launches += 1;
+        // the kernel for weak gauge fields while the lattice's last observables allow it
+        const bool weak = L.weak && fused2_weak_ok(fused2_default_variant(), L.N);
+        weak_launches += weak;
         return launch_fused2_step(v, L.N, host_kick_coef32(L.cfg, n), host_kick_coef32(L.cfg, n + 1),
-                                  fused2_default_variant(), st);
+                                  fused2_default_variant(), st, weak);
     }
 
     // The launches of a round of R batched steps (R: the fewest steps any
@@ -456,8 +461,9 @@ struct Engine {
     }
 
     // Observables of one lattice at its current step (the whole-lattice pass on
-    // the step's tile walk; everything in FP64 if the near-cut list overflows).
-    ah_status diag(const Lat &L, ah_obs *out)
+    // the step's tile walk; everything in FP64 if the near-cut list overflows);
+    // they also choose the form of its next direct two-step launches.
+    ah_status diag(Lat &L, ah_obs *out)
     {
         TraceRange tr("batch diagnostics");
         const View<float> v = lat_view(L);
@@ -481,6 +487,7 @@ struct Engine {
         }
         if (e != cudaSuccess) return host_fail(AH_ERR_CUDA, cudaGetErrorString(e));
         host_fill_obs(L.cfg, L.step, L.nsites, *h_result, out);
+        L.weak = L.two && out->max_abs_theta <= kWeakTheta;
         return AH_OK;
     }
 };
@@ -602,6 +609,7 @@ extern "C" ah_status ah_batch_run_ex(const ah_config *cfgs, int32_t count, int32
         cudaEventDestroy(b);
         eng.use_graph = !(flags & AH_BATCH_NO_GRAPH);
         eng.launches = 0;
+        eng.weak_launches = 0;
         eng.rounds = 0;
     }
     (two ? eng.shape2 : eng.shape) = best;
@@ -655,6 +663,7 @@ extern "C" ah_status ah_batch_run_ex(const ah_config *cfgs, int32_t count, int32
         stats->shape = best;
         stats->rounds = eng.rounds;
         stats->launches = eng.launches;
+        stats->weak_field_launches = eng.weak_launches;
     }
     cleanup();
     return st;

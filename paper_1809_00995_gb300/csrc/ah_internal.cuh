@@ -156,6 +156,11 @@ int fused_default_variant();
 cudaError_t launch_fused2_step(const View2<float> &v, int N, const KickCoef<float> &c1, const KickCoef<float> &c2,
                                int variant, cudaStream_t st, bool weak = false);
 bool fused2_weak_ok(int variant, int N);
+// Largest max |theta| at the last whole-lattice observables for which the
+// two-step launches take the kernel specialised to weak gauge fields (half the
+// bound of its short sine/cosine forms, 2^-6, so the phases may double before
+// the next observables; beyond it the kernel stays correct, only slower).
+constexpr double kWeakTheta = 0x1p-7;
 int fused2_variant_count();
 const char *fused2_variant_name(int variant);
 int fused2_default_variant();

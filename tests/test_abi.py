@@ -33,7 +33,7 @@ def test_library_exports_every_declared_function():
 
 
 def test_abi_version_and_struct_layouts(tmp_path):
-    assert ah.ah_abi_version() == 5
+    assert ah.ah_abi_version() == 6
     src = tmp_path / "sz.c"
     src.write_text('#include "ah.h"\n#include <stdio.h>\n#include <stddef.h>\n'
                    'int main(void){printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\\n", sizeof(ah_config), sizeof(ah_obs),'

@@ -210,8 +210,9 @@ def test_batch_1024cubed_light_cone_windows():
     and autotuned shapes, beside a small lattice stepped in pairs by the
     persistent two-step pass and one stepped one step per launch: after 20 steps
     three 16^3 windows (two across the periodic seam) equal the oracle's
-    evolution of the (16 + 2 * 20)^3 windows of the same initial lattice; the
-    small lattices equal the oracle whole."""
+    evolution of the (16 + 2 * 20)^3 windows of the same initial lattice (the
+    big lattice's passes take the kernel for weak gauge fields, as the bench's
+    do); the small lattices equal the oracle whole."""
     N, k, b = 1024, 20, 16
     big = short_config(N, ah.AH_MATTER, 1.0, 3, k, diag_every=0)
     # the 24^3 lattice is paired too (batched two-step pass); the 13^3 one takes
@@ -221,8 +222,11 @@ def test_batch_1024cubed_light_cone_windows():
     cfgs = [big] + small
     orgs = [(1016, 5, 1019), (300, 1010, 7), (511, 512, 640)]
     wins = [(0, *o, b, b, b) for o in orgs] + [(1, 0, 0, 0, 24, 24, 24), (2, 0, 0, 0, 13, 13, 13)]
-    series, _, fields = ah.ah_batch_run_ex(cfgs, wins, flags=ah.AH_BATCH_TWO_STEP | ah.AH_BATCH_AUTOTUNE,
-                                           series_cap=2)
+    series, st, fields = ah.ah_batch_run_ex(cfgs, wins, flags=ah.AH_BATCH_TWO_STEP | ah.AH_BATCH_AUTOTUNE,
+                                            series_cap=2)
+    # the observables at step 0 found max |theta| = 0: all ten passes of the
+    # 1024^3 lattice take the kernel for weak gauge fields
+    assert st["weak_field_launches"] == k // 2
     for w, org in enumerate(orgs):
         M = b + 2 * k
         ref, _ = oracle_fields(big, k, M=M, origin=[(o - k) % N for o in org])
@@ -244,8 +248,9 @@ def test_batch_large_paired_lattice_ending_before_the_others():
     big = short_config(N, ah.AH_RADIATION, 0.0, 8, k, diag_every=0)
     small = short_config(20, ah.AH_MATTER, 1.0, 9, 3 * k, diag_every=4)
     org = (508, 250, 3)
-    series, _, fields = ah.ah_batch_run_ex([big, small], [(0, *org, b, b, b), (1, 0, 0, 0, 20, 20, 20)],
-                                           flags=ah.AH_BATCH_TWO_STEP, series_cap=16)
+    series, st, fields = ah.ah_batch_run_ex([big, small], [(0, *org, b, b, b), (1, 0, 0, 0, 20, 20, 20)],
+                                            flags=ah.AH_BATCH_TWO_STEP, series_cap=16)
+    assert st["weak_field_launches"] == k // 2
     ref, _ = oracle_fields(big, k, M=b + 2 * k, origin=[(o - k) % N for o in org])
     assert max(rel_err(fields[0], ref[:, k:k + b, k:k + b, k:k + b])) <= TOL32
     ref_small, _ = oracle_fields(small, 3 * k)

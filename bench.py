@@ -575,6 +575,11 @@ def main():
                        "parallelism": "replicas" if world > 1 else "single"},
             "hbm_gbs_effective": achieved,
             "roofline": roofline,
+            # the rest of a bench step: one whole-lattice diagnostics pass (k_fused_diag
+            # tile walk, ordered sum, near-cut fix-up) and its read-back to the host
+            "diag_pass": {"ms_per_pass": (t_ms - step_ms) / a.steps, "share_of_time": 1.0 - step_ms / t_ms,
+                          "bound": "issue (FP32 arithmetic of the estimators, windings and double-float "
+                                   "Gauss residual; one read of the state)"},
             "cpu_baseline": cpu,
             "plain_fp64": plain,
             "e2e": {"value": e2e_value, "unit": "site-updates/s", "h2d_bytes_per_step": 0,
